@@ -1,0 +1,201 @@
+"""FP64 CPU oracle for the MD hot path -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline arm may import this
+package.  It wraps ``md_oracle.c`` (plain C, FP64, OpenMP over particles) through ctypes and
+shares no code with the CUDA path.  See ``md_oracle.c`` for the definitions and the paper
+passages each routine follows.
+
+Every function takes numpy arrays and returns numpy arrays; nothing here touches a GPU.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import sys
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "md_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+NVE, NVT = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile md_oracle.c into liboracle.so next to it (gcc, OpenMP, no FMA contraction)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           "-std=c11", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB)
+        d, i, f = C.POINTER(C.c_double), C.POINTER(C.c_int), C.POINTER(C.c_float)
+        L.or_version.restype = C.c_int
+        L.or_get_threads.restype = C.c_int
+        L.or_set_threads.argtypes = [C.c_int]
+        L.or_pair.argtypes = [C.c_double] * 4 + [d, d]
+        sig_f = [C.c_int, d, i, C.c_double, C.c_int, d, d, d, d, d, d, d]
+        L.or_forces.argtypes = sig_f
+        L.or_forces_cells.argtypes = sig_f
+        L.or_forces_subset.argtypes = [C.c_int, d, i, C.c_double, C.c_int, d, d, d, C.c_int, i, d,
+                                       d, d]
+        L.or_run.argtypes = [C.c_int, d, d, i, C.c_double, C.c_int, d, d, d, d, C.c_int,
+                             C.c_double, C.c_double, C.c_double, d, C.c_int, d, C.c_int]
+        L.or_neighbors_fp64.argtypes = [C.c_int, d, i, C.c_double, C.c_int, d, C.c_int, i, i]
+        L.or_neighbors_fp32.argtypes = [C.c_int, f, i, C.c_float, C.c_float, C.c_int, f, C.c_int,
+                                        i, i]
+        for name in ("or_pair", "or_set_threads"):
+            getattr(L, name).restype = None
+        for name in ("or_forces", "or_forces_cells", "or_forces_subset", "or_run",
+                     "or_neighbors_fp64", "or_neighbors_fp32"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _p(a, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype))
+
+
+def _params(model):
+    eps = np.ascontiguousarray(model.eps, dtype=np.float64).ravel()
+    sig = np.ascontiguousarray(model.sigma, dtype=np.float64).ravel()
+    rc = np.ascontiguousarray(model.rc, dtype=np.float64).ravel()
+    mass = np.ascontiguousarray(model.mass, dtype=np.float64).ravel()
+    return int(model.n_types), eps, sig, rc, mass
+
+
+def set_threads(n: int) -> None:
+    lib().or_set_threads(int(n))
+
+
+def threads() -> int:
+    return int(lib().or_get_threads())
+
+
+def pair(r: float, eps: float, sigma: float, rc: float):
+    """(u_SP(r), |F|(r)) for one pair at distance r; F > 0 is repulsive."""
+    u, fm = C.c_double(), C.c_double()
+    lib().or_pair(r, eps, sigma, rc, C.byref(u), C.byref(fm))
+    return u.value, fm.value
+
+
+def forces(pos, types, L, model, cells: bool = False):
+    """Forces (N,3), u_i (N,), w_i (N,), U, W at positions pos (any periodic image)."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    types = np.ascontiguousarray(types, dtype=np.int32)
+    n = pos.shape[0]
+    nt, eps, sig, rc, _ = _params(model)
+    f = np.zeros((n, 3)); u = np.zeros(n); w = np.zeros(n); uw = np.zeros(2)
+    fn = lib().or_forces_cells if cells else lib().or_forces
+    r = fn(n, _p(pos, C.c_double), _p(types, C.c_int), float(L), nt, _p(eps, C.c_double),
+           _p(sig, C.c_double), _p(rc, C.c_double), _p(f, C.c_double), _p(u, C.c_double),
+           _p(w, C.c_double), _p(uw, C.c_double))
+    if r:
+        raise ValueError(f"or_forces failed ({r})")
+    return f, u, w, float(uw[0]), float(uw[1])
+
+
+def forces_subset(pos, types, L, model, idx):
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    types = np.ascontiguousarray(types, dtype=np.int32)
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    n, k = pos.shape[0], idx.shape[0]
+    nt, eps, sig, rc, _ = _params(model)
+    f = np.zeros((k, 3)); u = np.zeros(k); w = np.zeros(k)
+    r = lib().or_forces_subset(n, _p(pos, C.c_double), _p(types, C.c_int), float(L), nt,
+                               _p(eps, C.c_double), _p(sig, C.c_double), _p(rc, C.c_double), k,
+                               _p(idx, C.c_int), _p(f, C.c_double), _p(u, C.c_double),
+                               _p(w, C.c_double))
+    if r:
+        raise ValueError(f"or_forces_subset failed ({r})")
+    return f, u, w
+
+
+class Run:
+    """Leapfrog NVE / Nose-Hoover NVT trajectory held in FP64 (unwrapped positions)."""
+
+    LOG_COLS = ("U", "W", "K_minus", "K_plus", "xi", "xi_int", "px", "py", "pz", "H")
+
+    def __init__(self, pos, vel, types, L, model, integrator="nve", dt=0.005, T=1.0, tau=0.2,
+                 cells=False):
+        self.pos = np.array(pos, dtype=np.float64, order="C", copy=True)
+        self.vel = np.array(vel, dtype=np.float64, order="C", copy=True)
+        self.types = np.ascontiguousarray(types, dtype=np.int32)
+        self.L = float(L)
+        self.model = model
+        self.integrator = NVT if integrator in ("nvt", NVT) else NVE
+        self.dt, self.T, self.tau = float(dt), float(T), float(tau)
+        self.cells = bool(cells)
+        self.state = np.zeros(4)   # xi, K_{n-1/2}, sum xi dt, have_K
+
+    def run(self, nsteps: int) -> np.ndarray:
+        n = self.pos.shape[0]
+        nt, eps, sig, rc, mass = _params(self.model)
+        log = np.zeros((max(nsteps, 1), 10))
+        r = lib().or_run(n, _p(self.pos, C.c_double), _p(self.vel, C.c_double),
+                         _p(self.types, C.c_int), self.L, nt, _p(eps, C.c_double),
+                         _p(sig, C.c_double), _p(rc, C.c_double), _p(mass, C.c_double),
+                         self.integrator, self.dt, self.T, self.tau, _p(self.state, C.c_double),
+                         int(nsteps), _p(log, C.c_double), int(self.cells))
+        if r:
+            raise ValueError(f"or_run failed ({r})")
+        return log[:nsteps]
+
+
+def neighbors_fp64(pos, types, L, model, skin, maxn=None):
+    """Brute-force neighbour sets in FP64: list of sorted int arrays, one per particle."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    types = np.ascontiguousarray(types, dtype=np.int32)
+    n = pos.shape[0]
+    nt, _, _, rc, _ = _params(model)
+    thr2 = np.ascontiguousarray((rc + skin) ** 2)
+    maxn = n if maxn is None else maxn
+    counts = np.zeros(n, dtype=np.int32)
+    lst = np.zeros((n, max(maxn, 1)), dtype=np.int32)
+    r = lib().or_neighbors_fp64(n, _p(pos, C.c_double), _p(types, C.c_int), float(L), nt,
+                                _p(thr2, C.c_double), maxn, _p(counts, C.c_int), _p(lst, C.c_int))
+    if r:
+        raise ValueError(f"or_neighbors_fp64 failed ({r})")
+    return [lst[i, :min(counts[i], maxn)].copy() for i in range(n)], counts
+
+
+def fp32_threshold(model, skin):
+    """(float)((rc_ab + s)^2) per type pair: the FP32 neighbour threshold."""
+    return ((np.asarray(model.rc, dtype=np.float64) + skin) ** 2).astype(np.float32).ravel()
+
+
+def neighbors_fp32(posf, types, L, model, skin, maxn=None):
+    """Brute-force neighbour sets in the bit-defined FP32 arithmetic (see md_oracle.c)."""
+    posf = np.ascontiguousarray(posf, dtype=np.float32)
+    types = np.ascontiguousarray(types, dtype=np.int32)
+    n = posf.shape[0]
+    nt = int(model.n_types)
+    thr2 = np.ascontiguousarray(fp32_threshold(model, skin))
+    maxn = n if maxn is None else maxn
+    counts = np.zeros(n, dtype=np.int32)
+    lst = np.zeros((n, max(maxn, 1)), dtype=np.int32)
+    Lf = np.float32(L)
+    invLf = np.float32(1.0 / float(L))
+    r = lib().or_neighbors_fp32(n, _p(posf, C.c_float), _p(types, C.c_int), C.c_float(Lf),
+                                C.c_float(invLf), nt, _p(thr2, C.c_float), maxn,
+                                _p(counts, C.c_int), _p(lst, C.c_int))
+    if r:
+        raise ValueError(f"or_neighbors_fp32 failed ({r})")
+    return [lst[i, :min(counts[i], maxn)].copy() for i in range(n)], counts
+
+
+if __name__ == "__main__":   # build only
+    print(build(force="--force" in sys.argv))

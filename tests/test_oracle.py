@@ -1,0 +1,284 @@
+"""Pins for the FP64 CPU oracle: it is checked against facts fixed by the physics and mathematics,
+never against itself.
+
+Each test targets a plausible mistake:
+  - LJ minimum / value at sigma / shift value        -> dropped term, wrong power, wrong shift
+  - two particles across the periodic boundary       -> wrong min-image sign or direction of force
+  - finite differences F = -grad U                   -> force/energy sign or factor mismatch
+  - virial vs dU/dlambda                             -> wrong 1/3, wrong sign of W
+  - perfect fcc vs lattice-shell enumeration         -> wrong 1/2, self term, double/missing pairs
+  - Newton's third law, translation/permutation      -> asymmetric indexing, transposed operands
+  - linked cells == double loop                      -> cell bookkeeping of the large-N routine
+  - neighbour sets vs 27-image brute force           -> min-image or strict "<" of the list rule
+  - leapfrog order-2 error, reversibility, momentum  -> first-order update, stale velocity
+  - Nose-Hoover: <T> -> T0, H conserved, tau -> inf == NVE -> thermostat sign or scaling
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+KA = synth.ka_model()
+LJ = synth.lj_model()
+
+
+# --------------------------------------------------------------------------------------------
+# Pair potential closed forms
+# --------------------------------------------------------------------------------------------
+
+# Textbook value of the LJ energy at r = 2.5 sigma: 4 (2.5^-12 - 2.5^-6) = -0.016316891136 eps.
+U_RC_25 = -0.016316891136
+
+
+@pytest.mark.parametrize("a,b", [(0, 0), (0, 1), (1, 1)])
+def test_lj_minimum_has_zero_force(a, b):
+    eps, sig, rc = KA.eps[a, b], KA.sigma[a, b], KA.rc[a, b]
+    u, f = oracle.pair(2.0 ** (1.0 / 6.0) * sig, eps, sig, rc)
+    assert abs(f) < 1e-12 * eps / sig
+    # depth -eps, shifted by -u(rc); every KA pair has rc = 2.5 sigma
+    assert u == pytest.approx(-eps - eps * U_RC_25, rel=1e-12)
+
+
+def test_value_at_sigma_and_cutoff():
+    u, f = oracle.pair(1.0, 1.0, 1.0, 2.5)
+    assert u == pytest.approx(-U_RC_25, rel=1e-10)         # u(sigma) = 0, minus the shift
+    assert f == pytest.approx(24.0, rel=1e-13)              # |F|(sigma) = 24 eps / sigma
+    u_in, f_in = oracle.pair(2.5 - 1e-10, 1.0, 1.0, 2.5)
+    assert abs(u_in) < 1e-9                                 # continuous at rc (shifted potential)
+    assert f_in < 0 and f_in == pytest.approx(-0.0390, rel=0.01)   # SP leaves the force jump
+    assert oracle.pair(2.5, 1.0, 1.0, 2.5) == (0.0, 0.0)    # strictly r < rc
+
+
+def test_two_particles_across_boundary():
+    L = 8.0
+    r = 1.05
+    pos = np.array([[0.3, 4.0, 4.0], [L - (r - 0.3), 4.0, 4.0]])
+    f, u, w, U, W = oracle.forces(pos, np.zeros(2, np.int32), L, LJ)
+    ue, fm = oracle.pair(r, 1.0, 1.0, 2.5)
+    # r < 2^(1/6): repulsive; the partner sits at -x across the boundary, so particle 0 is pushed +x
+    assert fm > 0
+    assert f[0, 0] == pytest.approx(fm, rel=1e-12) and f[1, 0] == pytest.approx(-fm, rel=1e-12)
+    assert np.abs(f[:, 1:]).max() < 1e-12
+    assert U == pytest.approx(ue, rel=1e-12)
+    assert u[0] == pytest.approx(ue / 2, rel=1e-12)
+    assert W == pytest.approx(r * fm / 3.0, rel=1e-12)
+
+
+# --------------------------------------------------------------------------------------------
+# Many-body consistency
+# --------------------------------------------------------------------------------------------
+
+def _ka_small(n=200, rho=1.0, seed=7):
+    return synth.ka_random_state(n, rho, 1.0, seed)
+
+
+def test_force_is_minus_gradient_of_energy():
+    s = _ka_small()
+    f, *_ = oracle.forces(s.pos, s.types, s.L, KA)
+    h = 1e-6
+    rng = np.random.default_rng(1)
+    for i in rng.choice(s.n, 8, replace=False):
+        for c in range(3):
+            p = s.pos.copy(); p[i, c] += h
+            up = oracle.forces(p, s.types, s.L, KA)[3]
+            p[i, c] -= 2 * h
+            um = oracle.forces(p, s.types, s.L, KA)[3]
+            fd = -(up - um) / (2 * h)
+            assert fd == pytest.approx(f[i, c], abs=2e-6 * max(1.0, np.abs(f[i]).max()))
+
+
+def test_virial_is_volume_derivative():
+    s = _ka_small()
+    _, _, _, U0, W = oracle.forces(s.pos, s.types, s.L, KA)
+    h = 1e-6
+    up = oracle.forces(s.pos * (1 + h), s.types, s.L * (1 + h), KA)[3]
+    um = oracle.forces(s.pos * (1 - h), s.types, s.L * (1 - h), KA)[3]
+    dU = (up - um) / (2 * h)
+    assert W == pytest.approx(-dU / 3.0, rel=1e-6, abs=1e-6 * abs(U0))
+
+
+def test_newton_third_law():
+    s = _ka_small()
+    f, *_ = oracle.forces(s.pos, s.types, s.L, KA)
+    assert np.abs(f.sum(axis=0)).max() < 1e-12 * np.abs(f).sum()
+
+
+def test_translation_and_permutation_invariance():
+    s = _ka_small()
+    f, u, w, U, W = oracle.forces(s.pos, s.types, s.L, KA)
+    shift = np.array([1.234, -3.21, 7.77])
+    f2, u2, w2, U2, W2 = oracle.forces(np.mod(s.pos + shift, s.L), s.types, s.L, KA)
+    np.testing.assert_allclose(f2, f, rtol=1e-9, atol=1e-9)
+    assert U2 == pytest.approx(U, rel=1e-12)
+    perm = np.random.default_rng(3).permutation(s.n)
+    f3, u3, w3, U3, W3 = oracle.forces(s.pos[perm], s.types[perm], s.L, KA)
+    np.testing.assert_allclose(f3, f[perm], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(u3, u[perm], rtol=1e-12, atol=1e-14)
+    assert W3 == pytest.approx(W, rel=1e-12)
+
+
+def _fcc_shell_sums(a, rc):
+    """u_i and w_i of a perfect fcc lattice (cubic constant a) by enumerating lattice vectors.
+
+    fcc = integer triples (in units of a/2) with an even coordinate sum; each vector within rc is
+    one neighbour.  Uses only the pair function, never the many-body routine.
+    """
+    m = int(math.ceil(2 * rc / a)) + 1
+    u = w = 0.0
+    for i, j, k in itertools.product(range(-m, m + 1), repeat=3):
+        if (i, j, k) == (0, 0, 0) or (i + j + k) % 2:
+            continue
+        r = 0.5 * a * math.sqrt(i * i + j * j + k * k)
+        if r < rc:
+            e, fm = oracle.pair(r, 1.0, 1.0, rc)
+            u += 0.5 * e
+            w += 0.5 * fm * r / 3.0
+    return u, w
+
+
+def test_perfect_fcc_matches_lattice_shell_sum():
+    k = 6
+    L = synth.box_edge(4 * k ** 3, 0.8442)
+    pos = synth.fcc_sites(k, L)
+    f, u, w, U, W = oracle.forces(pos, np.zeros(len(pos), np.int32), L, LJ)
+    assert np.abs(f).max() < 1e-10                        # zero by symmetry
+    assert np.ptp(u) < 1e-12 and np.ptp(w) < 1e-12        # all sites equivalent
+    us, ws = _fcc_shell_sums(L / k, 2.5)
+    assert u[0] == pytest.approx(us, rel=1e-12)
+    assert w[0] == pytest.approx(ws, rel=1e-12)
+    assert U == pytest.approx(len(pos) * us, rel=1e-12)
+
+
+def test_linked_cells_equal_double_loop():
+    s = synth.ka_random_state(2000, 1.2, 0.8, 11)
+    a = oracle.forces(s.pos, s.types, s.L, KA)
+    b = oracle.forces(s.pos, s.types, s.L, KA, cells=True)
+    np.testing.assert_allclose(b[0], a[0], rtol=0, atol=1e-11 * np.abs(a[0]).max())
+    assert b[3] == pytest.approx(a[3], rel=1e-12)
+    assert b[4] == pytest.approx(a[4], rel=1e-11)
+
+
+def test_subset_matches_full():
+    s = _ka_small()
+    f, u, w, *_ = oracle.forces(s.pos, s.types, s.L, KA)
+    idx = np.array([0, 5, 77, s.n - 1])
+    fs, us, ws = oracle.forces_subset(s.pos, s.types, s.L, KA, idx)
+    np.testing.assert_array_equal(fs, f[idx])
+    np.testing.assert_array_equal(us, u[idx])
+
+
+# --------------------------------------------------------------------------------------------
+# Neighbour sets
+# --------------------------------------------------------------------------------------------
+
+def _brute_27_images(pos, types, L, model, skin):
+    """Independent brute force: nearest of the 27 periodic images, no rounding formula."""
+    n = len(pos)
+    imgs = np.array(list(itertools.product((-1, 0, 1), repeat=3)), dtype=np.float64) * L
+    out = []
+    for i in range(n):
+        d = pos[None, :, :] + imgs[:, None, :] - pos[i][None, None, :]
+        d2 = (d * d).sum(axis=2).min(axis=0)
+        thr = (model.rc[types[i], types] + skin) ** 2
+        ok = d2 < thr
+        ok[i] = False
+        out.append(np.nonzero(ok)[0])
+    return out
+
+
+def test_neighbors_match_image_enumeration():
+    s = synth.ka_random_state(150, 0.9, 1.0, 5)
+    got, counts = oracle.neighbors_fp64(s.pos, s.types, s.L, KA, 0.3)
+    ref = _brute_27_images(s.pos, s.types, s.L, KA, 0.3)
+    for i in range(s.n):
+        np.testing.assert_array_equal(got[i], ref[i])
+    # full list: symmetric
+    pairs = {(i, int(j)) for i in range(s.n) for j in got[i]}
+    assert all((j, i) in pairs for (i, j) in pairs)
+
+
+def test_neighbors_fp32_agree_with_fp64_away_from_threshold():
+    s = synth.ka_random_state(1000, 1.2, 1.0, 9)
+    posf = s.pos.astype(np.float32)
+    n64, _ = oracle.neighbors_fp64(posf.astype(np.float64), s.types, s.L, KA, 0.3)
+    n32, _ = oracle.neighbors_fp32(posf, s.types, s.L, KA, 0.3)
+    near = 0
+    for i in range(s.n):
+        a, b = set(n64[i].tolist()), set(n32[i].tolist())
+        for j in a ^ b:
+            d = posf[j].astype(np.float64) - posf[i]
+            d -= s.L * np.round(d / s.L)
+            thr = (KA.rc[s.types[i], s.types[j]] + 0.3) ** 2
+            assert abs(d @ d - thr) < 1e-5 * thr
+            near += 1
+    assert near < 10
+
+
+# --------------------------------------------------------------------------------------------
+# Integrators
+# --------------------------------------------------------------------------------------------
+
+def _lj256():
+    s = synth.lj_fcc_state(256, 0.8442, 0.72, 1234)
+    return s
+
+
+def test_leapfrog_is_second_order():
+    s = _lj256()
+    spread = []
+    for dt, n in ((0.004, 100), (0.002, 200)):
+        r = oracle.Run(s.pos, s.vel, s.types, s.L, LJ, "nve", dt)
+        # start the half-step velocity consistently: v_{-1/2} = v_0 - dt/2 F_0
+        f0 = oracle.forces(s.pos, s.types, s.L, LJ)[0]
+        r.vel = np.ascontiguousarray(s.vel - 0.5 * dt * f0)
+        log = r.run(n)
+        E = log[:, 9]
+        spread.append(np.abs(E - E[0]).max())
+    ratio = spread[0] / spread[1]
+    assert 3.0 < ratio < 5.0, ratio
+
+
+def test_nve_momentum_and_energy():
+    s = _lj256()
+    r = oracle.Run(s.pos, s.vel, s.types, s.L, LJ, "nve", 0.005)
+    log = r.run(400)
+    p = log[:, 6:9]
+    assert np.abs(p).max() < 1e-11
+    E = log[:, 9] / s.n
+    assert np.abs(E - E[0]).max() < 2e-3
+
+
+def test_time_reversal():
+    s = _lj256()
+    dt, n = 0.005, 150
+    r = oracle.Run(s.pos, s.vel, s.types, s.L, LJ, "nve", dt)
+    r.run(n)
+    f = oracle.forces(r.pos, s.types, s.L, LJ)[0]
+    back = oracle.Run(r.pos, -(r.vel + dt * f), s.types, s.L, LJ, "nve", dt)
+    back.run(n)
+    assert np.abs(back.pos - s.pos).max() < 1e-9
+
+
+def test_nose_hoover_thermostats_and_conserves_H():
+    s = synth.ka_random_state(500, 1.2, 0.8, 21)
+    r = oracle.Run(s.pos, s.vel * 1.5, s.types, s.L, KA, "nvt", 0.0025, T=0.8, tau=0.2)
+    log = r.run(3000)
+    g = 3 * s.n - 3
+    Tk = (log[:, 2] + log[:, 3]) / g        # 2 K / g with K the half-step average
+    assert np.mean(Tk[1000:]) == pytest.approx(0.8, rel=0.05)
+    H = log[:, 9]
+    U = log[:, 0]
+    assert np.ptp(H[500:]) < 0.05 * np.ptp(U[500:])
+
+
+def test_nose_hoover_with_huge_tau_is_nve():
+    s = _lj256()
+    a = oracle.Run(s.pos, s.vel, s.types, s.L, LJ, "nve", 0.005)
+    b = oracle.Run(s.pos, s.vel, s.types, s.L, LJ, "nvt", 0.005, T=0.72, tau=1e9)
+    a.run(50)
+    b.run(50)
+    assert np.abs(a.pos - b.pos).max() < 1e-12
