@@ -1,0 +1,466 @@
+"""Benchmark: particle-timesteps/s of the MD hot path on GB300 (one JSON line on rank 0).
+
+Workload (default, N=1): the batched Kob-Andersen ensemble -- 512 independent replicas with
+N_r drawn uniformly from 512..4096 (seed 1004), rho = 1.2, Nose-Hoover NVT at T = 0.8,
+dt = 0.0025, skin 0.3, CUDA-graph blocks of 100 steps, kernel shape chosen by the autotuner.
+One bench step = one MD timestep of every replica (force + integrate + skin check + on-device
+rebuild where needed + FP64 reductions).  Inputs are synthetic (seeded), resident in HBM.
+The ensemble's working set (neighbour list ~0.45 GB) exceeds the 129 MB L2, so no flush is
+needed between timed steps.
+
+Also reported in the same line: the same replicas run one after another with plain kernel
+launches (the baseline of the batched form), the single-system workloads (KA N = 8000 NVT and
+LJ N = 131072 NVE, L2-flushed between individually timed steps), the dominant kernel's roofline
+position, an end-to-end number through the C ABI with host buffers, and the FP64 CPU oracle timed
+on a bounded sample (cpu_baseline).
+
+Multi-GPU (torchrun): replicas only -- each rank runs its own ensemble (seeds offset by rank), no
+collective on the data path; value = all ranks' particle-steps / max rank time ("weak").
+
+--impl reference times the FP64 CPU oracle (the plain O(N^2) definition) on a bounded sample
+of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "particle-timesteps/s (single system & batched replicas) vs plain launches, 1 GB300"
+UNIT = "particle-steps/s"
+GRAPH_BLOCK = 100
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ------------------------------------------------------------------------------ clocks sampler
+
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = str(gpu_index)
+        try:   # nvidia-smi numbers GPUs physically; address ours by UUID
+            import torch
+
+            u = str(torch.cuda.get_device_properties(gpu_index).uuid)
+            self.idx = u if u.startswith("GPU-") else "GPU-" + u
+        except Exception:
+            pass
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.idx, f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        except OSError:
+            return out
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if sm:
+            out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(mx), reasons=sorted(reasons),
+                       samples=len(sm))
+        os.unlink(self.path)
+        return out
+
+
+# ------------------------------------------------------------------------------ helpers
+
+def ensemble(rank: int, replicas: int | None = None):
+    wl = synth.workload("ka_ensemble512", replicas=replicas)
+    if rank:
+        sizes = [s.n for s in wl.states]
+        wl.states = [synth.ka_random_state(n, 1.2, wl.T, synth.replica_seed(1004 + 1000 * rank, r))
+                     for r, n in enumerate(sizes)]
+    return wl
+
+
+def make_sim(wl, stream, precision="mixed"):
+    from paper_1506_05094_gb300 import Sim
+
+    sim = Sim.from_model(wl.model, wl.states, skin=wl.skin, precision=precision, stream=stream)
+    sim.set_integrator(wl.integrator, dt=wl.dt, T=wl.T, tau=wl.tau)
+    for r, s in enumerate(wl.states):
+        sim.set_state(r, s.pos, s.types, s.vel)
+    return sim
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("md_kernels.cuh", "md_launch.inc", "md_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1506_05094_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_particle():
+    """DRAM bytes per particle of the step kernel from the committed ncu summary, if the kernel
+    source has not changed since it was taken (else None)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "k_step_traffic.json")) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if d.get("kernel_hash") != kernel_source_hash():
+        return None
+    return d
+
+
+def step_kernel_bytes(n_total: int, entries: int, precision: str) -> float:
+    """Algorithmic bytes of one fused step-kernel launch.
+
+    Per particle: neighbour indices 4 n_i; own position (16) + count (4); each neighbour
+    position counted once (16, reuse served on chip); velocity read+write (32); FP64 master
+    position read+write (48); new position mirror write (16); build position read (16).
+    FP64 mode doubles the Real4 quantities.
+    """
+    r4 = 32 if precision == "fp64" else 16
+    per = r4 + 4 + r4 + 2 * r4 + 48 + r4 + r4
+    return float(per * n_total + 4 * entries)
+
+
+def pick_block(steps: int) -> int:
+    """Graph block for a timed run of `steps`: 100 when it divides, else the largest even
+    divisor up to 200 (an odd count leaves one plain step)."""
+    if steps % GRAPH_BLOCK == 0:
+        return GRAPH_BLOCK
+    even = steps - (steps & 1)
+    for b in range(min(200, even), 1, -1):
+        if b % 2 == 0 and even % b == 0:
+            return b
+    return 2
+
+
+def time_steps(sim, stream_obj, steps: int):
+    import torch
+
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream_obj)
+    sim.step(steps)
+    e1.record(stream_obj)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def l2_flush_buffer():
+    import torch
+
+    return torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+
+def time_single_system(name, stream_obj, steps, warmup):
+    """Single system, each step timed alone with CUDA events and L2 flushed in between."""
+    import torch
+
+    wl = synth.workload(name)
+    sim = make_sim(wl, stream_obj.cuda_stream)
+    sim.autotune(os.path.join(ROOT, "paper_1506_05094_gb300", "tune_cache.txt"), 50)
+    sim.set_graph_block(0)
+    sim.step(max(warmup, 3))
+    flush = l2_flush_buffer()
+    tot = 0.0
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(steps):
+        with torch.cuda.stream(stream_obj):
+            flush.fill_(1.0)
+        e0.record(stream_obj)
+        sim.step(1)
+        e1.record(stream_obj)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+    # back-to-back graph replay of the same system (L2 stays warm: working set stated)
+    sim.set_graph_block(GRAPH_BLOCK)
+    sim.step(GRAPH_BLOCK)
+    ms_graph = time_steps(sim, stream_obj, 10 * GRAPH_BLOCK) / (10 * GRAPH_BLOCK)
+    st = sim.stats()
+    n = wl.n_total
+    out = {"workload": name, "n": n, "ms_per_step_flushed": tot / steps,
+           "value_flushed": n * steps / (tot / 1e3),
+           "ms_per_step_graph_l2_warm": ms_graph, "value_graph_l2_warm": n / (ms_graph / 1e3),
+           "tuning": list(sim.get_tuning()), "rebuild_passes": st["rebuild_passes"]}
+    sim.close()
+    del flush
+    return out
+
+
+def cpu_baseline(wl, max_seconds=15.0):
+    """The FP64 oracle (O(N^2) plain definition, OpenMP) on a bounded sample of the workload."""
+    import oracle
+
+    threads = oracle.threads()
+    done_ps, spent = 0, 0.0
+    picked = []
+    for s in wl.states:
+        run = oracle.Run(s.pos, s.vel, s.types, s.L, wl.model, wl.integrator, wl.dt, T=wl.T,
+                         tau=wl.tau)
+        t0 = time.perf_counter()
+        run.run(2)
+        dt = time.perf_counter() - t0
+        done_ps += 2 * s.n
+        spent += dt
+        picked.append(s.n)
+        if spent >= max_seconds:
+            break
+    return {"value": done_ps / spent, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{len(picked)} replicas (N={picked[0]}..), 2 NVT steps each, O(N^2) FP64",
+            "seconds": spent}
+
+
+# ------------------------------------------------------------------------------ reference arm
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+
+    wl = synth.workload("ka_ensemble512", replicas=4)
+    threads = oracle.threads()
+    runs = [oracle.Run(s.pos, s.vel, s.types, s.L, wl.model, wl.integrator, wl.dt, T=wl.T,
+                       tau=wl.tau) for s in wl.states]
+    n_sample = sum(s.n for s in wl.states)
+    for _ in range(args.warmup):
+        for r in runs:
+            r.run(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for r in runs:
+            r.run(1)
+    sec = time.perf_counter() - t0
+    value = n_sample * args.steps / sec
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": "KA ensemble: first 4 of the 512 replicas (N=%s), NVT T=0.8"
+                                   % [s.n for s in wl.states], "sample_particles": n_sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"4 replicas, {args.steps} steps, O(N^2) FP64"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------ main arm
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip single-system/e2e/cpu legs")
+    ap.add_argument("--replicas", type=int, default=None, help="trim the ensemble (profiling)")
+    ap.add_argument("--tuning", default=None, help="tp,block,reach: skip the autotuner")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    from paper_1506_05094_gb300 import md as mdmod  # noqa: F401  (fails loudly if not built)
+
+    stream = torch.cuda.Stream(device=local)
+    wl = ensemble(rank, args.replicas)
+    n_total = wl.n_total
+    sim = make_sim(wl, stream.cuda_stream)
+    if args.tuning:
+        tuning = tuple(int(x) for x in args.tuning.split(","))
+        sim.set_tuning(*tuning)
+    else:
+        tuning = sim.autotune(os.path.join(ROOT, "paper_1506_05094_gb300", "tune_cache.txt"), 50)
+    gb = pick_block(args.steps)
+    sim.set_graph_block(gb)
+    sim.step(gb)                     # capture the graph (setup, untimed)
+    sim.step(args.warmup)            # warm-up steps, untimed
+    st0 = sim.stats()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    with Clocks(local) as ck:
+        ms = time_steps(sim, stream, args.steps)
+    barrier()
+    clocks = ck.summary()
+    st1 = sim.stats()
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = n_total * world * args.steps / (ms_max / 1e3)
+    passes = st1["rebuild_passes"] - st0["rebuild_passes"]
+    # graph replays: one arm kernel + gb step kernels + 6 rebuild kernels per executed IF body;
+    # an odd K ends with one plain step (its 6 rebuild kernels launch and exit if not needed)
+    n_graphs = args.steps // gb
+    rem = args.steps - n_graphs * gb
+    gpu_launches = args.steps + n_graphs + 6 * passes + 6 * rem
+
+    # dominant kernel: fused step kernel, plain launches with CUDA events on the sim's stream
+    prof = sim.profile(50)
+    peaks, peak_kind = _peaks()
+    bytes_launch = step_kernel_bytes(n_total, prof["neighbor_entries"], "mixed")
+    achieved = bytes_launch / (prof["step_kernel_ms"] * 1e-3) / 1e9
+    tr = traffic_per_particle()
+    traffic = None if tr is None else tr["dram_bytes_per_particle"] * n_total
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                "kernel": "k_step (force+integrate+check+reductions)",
+                "step_kernel_ms": prof["step_kernel_ms"],
+                "algorithmic_bytes_per_launch": bytes_launch,
+                "peak_kind": f"{peak_kind} hbm_gbs (burst copy)",
+                "rebuild_pass_ms": prof["rebuild_ms"],
+                "rebuild_passes_per_step": prof["rebuild_fraction"]}
+
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        # e2e through the C ABI with host buffers: set_state (H2D) -> steps -> energies + state (D2H)
+        sim.set_graph_block(GRAPH_BLOCK)
+        host = [(s.pos, s.types, s.vel) for s in wl.states]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for r, (p, ty, v) in enumerate(host):
+            sim.set_state(r, p, ty, v)
+        sim.step(args.steps)
+        en = [sim.energies(r) for r in range(wl.states.__len__())]
+        outs = [sim.get_state(r) for r in range(len(wl.states))]
+        t1 = time.perf_counter()
+        del en, outs
+        h2d = n_total * (24 + 4 + 24)
+        d2h = n_total * (24 + 12 + 24) + len(wl.states) * 128
+        extras["e2e"] = {"value": n_total * args.steps / (t1 - t0), "unit": UNIT,
+                         "h2d_bytes_per_step": h2d / args.steps,
+                         "d2h_bytes_per_step": d2h / args.steps,
+                         "what": "md_set_state for all replicas, md_step(K), md_get_energies + "
+                                 "md_get_state for all replicas, host wall clock"}
+        # batched vs the same replicas one after another with plain launches
+        seq_steps = 20
+        from paper_1506_05094_gb300 import Sim
+        t_seq = 0.0
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for s in wl.states:
+            one = Sim.from_model(wl.model, [s], skin=wl.skin, stream=stream.cuda_stream)
+            one.set_integrator(wl.integrator, dt=wl.dt, T=wl.T, tau=wl.tau)
+            one.set_tuning(*tuning)
+            one.set_graph_block(0)
+            one.set_state(0, s.pos, s.types, s.vel)
+            one.step(2)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            one.step(seq_steps)
+            ev1.record(stream)
+            ev1.synchronize()
+            t_seq += ev0.elapsed_time(ev1)
+            one.close()
+        seq_value = n_total * seq_steps / (t_seq / 1e3)
+        extras["sequential_plain_launches"] = {"value": seq_value, "unit": UNIT,
+                                               "steps": seq_steps,
+                                               "batched_over_sequential": value / world / seq_value}
+        # single systems
+        extras["single_system"] = [time_single_system("ka8000", stream, 200, args.warmup),
+                                   time_single_system("lj131072", stream, 200, args.warmup)]
+        extras["cpu_baseline"] = cpu_baseline(wl)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": "KA ensemble: 512 replicas, N_r~U{512..4096} seed 1004, "
+                                       "rho=1.2, NVT T=0.8 dt=0.0025 skin=0.3",
+                           "particles_per_gpu": n_total, "replicas": len(wl.states),
+                           "graph_block": gb, "tuning_tp_block_reach": list(tuning),
+                           "precision": "FP32 pair math, FP64 positions and reductions",
+                           "l2": "no flush: neighbour list %.2f GB > 129 MB L2"
+                                 % (4.0 * st1["neighbor_entries"] / 1e9),
+                           "parallelism": f"replicas x{world}"},
+                "clocks": clocks, "gpu_launches": gpu_launches, "roofline": roofline}
+        line.update(extras)
+        if "e2e" not in line:
+            line["e2e"] = None
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,201 @@
+/*
+ * md.h -- C ABI of the GB300 molecular-dynamics hot path.
+ *
+ * One call of md_step advances every replica of an md_sim by leapfrog timesteps of a
+ * Lennard-Jones 12-6 pair potential with the shifted-potential cutoff, evaluated over a Verlet
+ * neighbour list that is rebuilt from a spatially sorted cell list whenever any particle of the
+ * replica has moved more than half the skin since the last build.  This is the method of
+ * Bailey et al., "RUMD: A general purpose molecular dynamics package optimized to utilize GPU
+ * hardware down to a few thousand particles":
+ *   - force, per-particle energy and virial over the neighbour list ........ Sec. 5, Fig. 2
+ *   - neighbour list of all pairs within rc + s, column-major, with skin s .. Sec. 4, Sec. 5
+ *   - rebuild when any particle moved more than s/2 (device-side flag) ..... Sec. 6 (O(N^2) text)
+ *   - cell-index binning, sort of all particle data by cell, list build .... Sec. 7, Fig. 4
+ *   - leapfrog NVE and Nose-Hoover NVT integrators .......................... Sec. 2
+ *   - shifted-potential cutoff ............................................... Sec. 2
+ *   - parameter search over threads per particle, block size, cell size ..... Appendix
+ *
+ * Conventions.
+ *   - Every function returns an md_status (0 = MD_OK).  Errors are sticky per md_sim: after a
+ *     failure of md_step / md_sync (MD_EUNSTABLE, MD_ECUDA, MD_ETIMEOUT) every later call that
+ *     needs the device returns the same code until md_destroy.  Argument errors (MD_EINVAL)
+ *     are not sticky.
+ *   - All array arguments are HOST pointers owned by the caller; getters copy out, setters copy
+ *     in.  The library owns every device buffer it allocates (cudaMalloc on the current
+ *     device at md_create time) and frees them in md_destroy.
+ *   - Particles of a replica are addressed in the caller's ("user") order 0..n_r-1 in every
+ *     getter and setter, whatever order the library keeps them in on the device.
+ *   - Positions are (n,3) row-major doubles; velocities (n,3) doubles holding v(t - dt/2) (the
+ *     leapfrog half step); images (n,3) int32 periodic image counters.
+ *   - Work is issued on the stream given by md_set_stream (default: a stream the library
+ *     creates).  md_step returns after the requested steps have completed on the device.
+ *   - Not thread-safe: one host thread per md_sim at a time.
+ */
+#ifndef GB300_MD_H
+#define GB300_MD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct md_sim md_sim;
+
+typedef enum {
+    MD_OK = 0,
+    MD_EINVAL = 1,     /* bad argument or violated precondition (no state change) */
+    MD_ENOMEM = 2,     /* device or host allocation failed */
+    MD_ECUDA = 3,      /* a CUDA runtime call failed (sticky) */
+    MD_EUNSTABLE = 4,  /* non-finite position or a displacement > L/4 in one step (sticky) */
+    MD_ETIMEOUT = 5,   /* a bounded device wait ran out (sticky) */
+    MD_ESTATE = 6      /* call out of order, e.g. md_step before md_set_state of every replica */
+} md_status;
+
+enum { MD_SHIFTED_POTENTIAL = 0 };              /* cutoff methods (Sec. 2 "Pair potentials") */
+enum { MD_MIXED = 0, MD_FP64 = 1 };             /* precision modes, see md_create */
+enum { MD_NVE_LEAPFROG = 0, MD_NVT_NOSE_HOOVER = 1 };
+
+/* LJ parameters of one (ordered) type pair; the matrix must be symmetric.  rc is absolute. */
+typedef struct {
+    double eps, sigma, rc;
+} md_pair;
+
+/* Thermodynamic record of the last completed step of one replica.  A completed step n evaluates
+ * the forces at r_n, so after s completed steps the record describes time index n = s - 1. */
+typedef struct {
+    long long step;      /* n = completed steps - 1; -1 before the first step */
+    int n;               /* particles in the replica */
+    double V;            /* box volume L^3 */
+    double U;            /* potential energy at r_n: sum_i u_i, u_i = 1/2 sum_j u_SP(r_ij) */
+    double W;            /* virial at r_n: 1/3 sum_{i<j} r_ij . F_ij */
+    double K;            /* kinetic energy at n: (K_{n-1/2} + K_{n+1/2}) / 2 */
+    double K_minus;      /* K_{n-1/2} */
+    double K_plus;       /* K_{n+1/2} */
+    double T_kin;        /* 2 K / (3n - 3) */
+    double P;            /* (n T_kin + W) / V */
+    double xi;           /* Nose-Hoover friction xi_n (0 for NVE) */
+    double xi_int;       /* sum_k xi_k dt */
+    double H;            /* U + K (+ g T0 (tau^2 xi^2 / 2 + xi_int) for NVT): conserved */
+    double sum_p[3];     /* total momentum of v_{n+1/2} */
+} md_energies;
+
+/* Counters kept by the runtime (host side; read after md_sync). */
+typedef struct {
+    long long steps;            /* completed steps */
+    long long rebuild_passes;   /* device rebuild passes (any replica rebuilt) */
+    long long replica_rebuilds; /* sum over replicas of list rebuilds */
+    long long overflows;        /* neighbour-list overflows recovered by doubling n_max */
+    int n_max;                  /* current neighbour-list capacity per particle */
+    int max_neighbors;          /* largest neighbour count at the most recent build */
+    int tp, block, reach;       /* threads per particle, threads per block, cell stencil reach */
+    int graph_block;            /* steps per captured CUDA graph (0 = plain launches) */
+    long long n_total;          /* particles over all replicas */
+    long long neighbor_entries; /* sum of neighbour counts at the most recent build */
+} md_stats;
+
+/* Average device durations measured with CUDA events by md_profile (milliseconds). */
+typedef struct {
+    double step_kernel_ms;       /* fused force + integrate + check + reduction kernel */
+    double rebuild_ms;           /* one full rebuild pass (bin, scan, scatter, sort, gather, build) */
+    double rebuild_fraction;     /* rebuild passes per step during the profiled steps */
+    long long neighbor_entries;  /* sum of neighbour counts (for algorithmic bytes) */
+    int steps;                   /* profiled steps */
+} md_timing;
+
+/* Create a simulation of n_replicas independent systems in cubic periodic boxes.
+ *   n_particles[r] >= 2, box[r] = edge L_r > 2 (rc_max + skin) (minimum image, Sec. 4);
+ *   params: n_types x n_types row-major LJ parameters (Sec. 2), symmetric, rc > 0, sigma > 0;
+ *   mass: n_types masses (NULL = all 1);  skin > 0 (Sec. 4: list holds pairs with r < rc + s);
+ *   cutoff_method: MD_SHIFTED_POTENTIAL;  precision: MD_MIXED (FP32 pair math and FP32
+ *   per-particle accumulation; FP64 master positions, image update and energy/virial/momentum
+ *   reductions) or MD_FP64 (every quantity in FP64).
+ * n_types <= 8, n_replicas >= 1.  On success *out owns device memory for all replicas. */
+int md_create(md_sim **out, int n_replicas, const int *n_particles, const double *box,
+              int n_types, const md_pair *params, const double *mass, double skin,
+              int cutoff_method, int precision);
+
+/* Integrator (Sec. 2): MD_NVE_LEAPFROG, or MD_NVT_NOSE_HOOVER with target T and relaxation time
+ * tau (friction update xi_n = xi_{n-1} + dt (K_{n-1/2}/K0 - 1)/tau^2, K0 = (3N-3) T / 2). */
+int md_set_integrator(md_sim *sim, int kind, double dt, double T, double tau);
+
+/* Load replica r: pos (n,3) in any periodic image (wrapped into [0,L) here, the wrap added to
+ * the image counters), type (n) in [0,n_types), vel (n,3) = v(t - dt/2), image (n,3) or NULL.
+ * Resets the replica's thermostat (xi = 0) and step record, and forces a list rebuild. */
+int md_set_state(md_sim *sim, int replica, const double *pos, const int *type, const double *vel,
+                 const int *image);
+
+/* Issue all device work on this cudaStream_t (e.g. torch.cuda.current_stream().cuda_stream). */
+int md_set_stream(md_sim *sim, void *cuda_stream);
+
+/* Advance all replicas by n_steps >= 0 timesteps (Fig. 2 force kernel fused with the
+ * integrator; rebuild of Fig. 4 on the device when the skin criterion fires).  Neighbour-list
+ * overflow is recovered inside the call (capacity doubled, list rebuilt, the step redone),
+ * as in Sec. 4.  Returns after the steps completed, or the first sticky error. */
+int md_step(md_sim *sim, long long n_steps);
+
+/* Wait for outstanding work; surfaces sticky device errors. */
+int md_sync(md_sim *sim);
+
+/* Copy replica r out in user order: pos (n,3) wrapped into [0,L), image (n,3), vel (n,3) =
+ * v(t - dt/2).  Any pointer may be NULL. */
+int md_get_state(md_sim *sim, int replica, double *pos, int *image, double *vel);
+
+/* Thermodynamic record of replica r (see md_energies). */
+int md_get_energies(md_sim *sim, int replica, md_energies *out);
+
+/* Test hook: forces f (n,3), u_i (n), w_i (n) at the CURRENT positions of replica r (rebuilding
+ * the list first if needed), user order; u_i = 1/2 sum_j u_SP, w_i = 1/6 sum_j r_ij . F_ij
+ * (Fig. 2: per-particle energy halved for the double counting).  Any output may be NULL. */
+int md_get_forces(md_sim *sim, int replica, double *f, double *u, double *w);
+
+/* Test hook: neighbour list of replica r at its most recent build, as user indices.  counts[n];
+ * nbrs (n, max_per_particle) row-major, each row in list order, unused slots -1.  Requires a
+ * prior md_step or md_get_forces (the list exists only after a build). */
+int md_get_neighbors(md_sim *sim, int replica, int max_per_particle, int *counts, int *nbrs);
+
+/* Kernel shape: tp in {1,2,4,8,16,32} threads per particle (Sec. 3 t_p), block threads per CTA
+ * (multiple of 32, tp <= block <= 1024), reach in {1,2,3}: cell edge >= (rc_max + skin)/reach
+ * with a (2 reach + 1)^3 stencil (Sec. 7 uses reach 2).  0 keeps the current value. */
+int md_set_tuning(md_sim *sim, int tp, int block, int reach);
+int md_get_tuning(md_sim *sim, int *tp, int *block, int *reach);
+
+/* Steps captured per CUDA graph replay (even, >= 2), or 0 for plain kernel launches with
+ * device-side early exit of the rebuild kernels (the baseline launch mode). */
+int md_set_graph_block(md_sim *sim, int steps);
+
+/* Parameter search of the Appendix, reduced to tp, block and reach: short timed runs from the
+ * current state (restored after every trial), single-minimum line searches with the break rules
+ * of the Appendix.  cache_path (may be NULL) is a text file of tuned parameters keyed by the
+ * user parameters and the GPU name; a hit skips the search.  The state is unchanged. */
+int md_autotune(md_sim *sim, const char *cache_path, int steps_per_trial);
+
+/* Runtime counters. */
+int md_get_stats(md_sim *sim, md_stats *out);
+
+/* Run n_steps with plain launches and a CUDA event pair around every kernel; report average
+ * durations.  Advances the simulation by n_steps (it is a real run). */
+int md_profile(md_sim *sim, int n_steps, md_timing *out);
+
+/* Per-step thermodynamic log on the device: capacity rows per replica (0 disables).  Each
+ * completed step n writes (n, U, W, K_minus, K_plus, xi, xi_int, H, p_x, p_y, p_z). */
+int md_set_log(md_sim *sim, int capacity);
+/* Copy up to max_rows most recent rows of replica r, oldest first, 11 doubles per row; the
+ * number of rows written is returned in *rows. */
+int md_get_log(md_sim *sim, int replica, int max_rows, double *out, int *rows);
+
+/* Bit-exact checkpoint: the full device state (positions, images, velocities, build positions,
+ * thermostat carry, step counters, pending rebuild flags) in user order.  Loading it into an
+ * md_sim created with the same arguments and tuning reproduces the uninterrupted trajectory
+ * bit for bit. */
+int md_checkpoint_size(md_sim *sim, size_t *bytes);
+int md_save_checkpoint(md_sim *sim, void *buf, size_t bytes);
+int md_load_checkpoint(md_sim *sim, const void *buf, size_t bytes);
+
+void md_destroy(md_sim *sim);
+const char *md_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GB300_MD_H */

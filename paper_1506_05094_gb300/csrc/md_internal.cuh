@@ -1,0 +1,154 @@
+// md_internal.cuh -- device-side data layout and kernel argument blocks shared by the kernels
+// and the host runtime of the GB300 MD path.  Not part of the public ABI.
+//
+// Layout (all per-particle arrays are indexed by the device's cell-sorted slot; replica r owns
+// slots [off_r, off_r + n_r), and the order inside a replica is (cell, user id)):
+//   pos[2]      : Real4 mirror of the positions, x,y,z plus the type in .w (float bits of the
+//                 int for FP32, the int's bits in the double for FP64); ping-pong by step parity
+//   xd,yd,zd    : FP64 master positions, wrapped into [0, L)
+//   img         : int4 periodic image counters (touched only when a particle wraps)
+//   vel         : Real4 velocities v(t - dt/2), .w unused
+//   id          : user index inside the replica
+//   pos_build   : Real4 positions at the last list build (rebuild check, Sec. 6)
+//   nbl         : int32 neighbour slots, column-major: neighbour k of slot i at nbl[k*ncap + i]
+//                 (Sec. 5: first neighbours of all particles contiguous, then second, ...)
+//   nnb         : int32 neighbour counts
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define MD_MAX_TYPES 8
+#define MD_MAX_PAIRS (MD_MAX_TYPES * MD_MAX_TYPES)
+#define MD_LOG_COLS 11
+#define MD_NRED 6   // reduced quantities per tile: U, W, K, px, py, pz
+
+template <typename R> struct V4T;
+template <> struct V4T<float> { typedef float4 t; };
+template <> struct V4T<double> { typedef double4_32a t; };
+
+// Per replica description (device array, read-only inside a step).
+struct SysDesc {
+    int off, n;            // first slot, particle count
+    int cell_off, nc;      // first cell, cells per box edge
+    int tile_off, ntiles;  // first tile of the step kernel, tile count
+    int reach;             // stencil half width in cells
+    int span;              // cells visited per dimension (min(2 reach + 1, nc))
+    double L, invL;
+    float Lf, invLf, cell_scale, pad;  // cell_scale = nc / L rounded to float
+    double K0;             // (3n - 3) T0 / 2
+};
+
+// Per type-pair LJ table (shifted potential, Sec. 2).
+//   u(r)   = c12 r^-12 - c6 r^-6 - ushift    (c12 = 4 eps sigma^12, c6 = 4 eps sigma^6)
+//   F_ij   = r^-2 (a12 r^-12 - a6 r^-6) r_ij (a12 = 12 c12, a6 = 6 c6)
+//   rc2    = rc^2,  thr2 = (rc + s)^2 (neighbour threshold)
+struct PairTab {
+    float rc2, c12, c6, ushift, a12, a6, thr2, pad;
+    double rc2d, c12d, c6d, ushiftd, a12d, a6d, thr2d, padd;
+};
+
+// Per replica thermostat carry and last-step record (FP64).
+struct Thermo {
+    double xi_prev;   // xi_{n-1}
+    double K_prev;    // K_{n-1/2}
+    double xi_int;    // sum_k xi_k dt
+    double U, W, K_minus, K_plus, xi, px, py, pz;
+    long long step;   // completed steps of this replica
+    long long rebuilds;
+};
+
+// Global control block.
+struct Ctrl {
+    int halt;           // nonzero: every kernel returns at once
+    int overflow;       // neighbour list overflowed at the last build
+    int unstable;       // non-finite or runaway displacement seen
+    int need_any;       // some replica needs a rebuild before the next step
+    int max_count;      // largest neighbour count seen by the most recent builds
+    unsigned int global_ticket;
+    long long step;     // completed steps (all replicas step together)
+    long long rebuild_passes;
+    unsigned long long nb_entries;  // sum of neighbour counts written by the last pass
+    int pad[2];
+};
+
+template <typename R> struct StepArgs {
+    typedef typename V4T<R>::t V4;
+    const V4 *pos_in;
+    V4 *pos_out;
+    double *xd, *yd, *zd;
+    V4 *vel;
+    int4 *img;
+    const V4 *pos_build;
+    const int *nbl;
+    const int *nnb;
+    long long ncap;           // column stride of nbl (= total slots)
+    const int *tile_rep;      // tile -> replica
+    const SysDesc *sys;
+    const PairTab *tab;
+    int ntypes;
+    int nrep;
+    double inv_mass[MD_MAX_TYPES];
+    double mass[MD_MAX_TYPES];
+    Thermo *th;
+    Ctrl *ctrl;
+    int *moved;               // per replica: some particle moved > s/2 this step
+    int *need;                // per replica: rebuild before the next step
+    unsigned int *rep_ticket; // per replica tile tickets
+    double *partial;          // per tile MD_NRED partial sums
+    double *log;              // MD_LOG_COLS doubles per (row, replica) or null
+    int log_cap;
+    int integrator;           // 0 NVE, 1 Nose-Hoover
+    double dt;
+    double T0;
+    double inv_tau2;
+    R half_skin2;             // (s/2)^2
+    int force_only;           // 1: write f_out / w_out, no integration and no bookkeeping
+    V4 *f_out;                // fx, fy, fz, u_i
+    R *w_out;
+    cudaGraphConditionalHandle next_handle;
+    int has_next;
+};
+
+template <typename R> struct RebuildArgs {
+    typedef typename V4T<R>::t V4;
+    V4 *pos;                 // current mirror (in/out, permuted)
+    const V4 *key;           // positions the cells and the list are built from (== pos normally)
+    int key_is_pos;
+    double *xd, *yd, *zd;
+    V4 *vel;
+    int4 *img;
+    int *id;
+    V4 *pos_build;
+    // scratch
+    V4 *tpos, *tkey;
+    double *txd, *tyd, *tzd;
+    V4 *tvel;
+    int4 *timg;
+    int *tid;
+    int *cell_of, *rank, *perm;
+    int *cell_start;         // Ctot + 1 entries
+    int *count;              // Ctot entries, zero between passes
+    const int *prep;         // slot -> replica
+    const int *crep;         // cell -> replica
+    int *nbl;
+    int *nnb;
+    long long ncap;
+    int nmax;
+    const SysDesc *sys;
+    const PairTab *tab;
+    int ntypes;
+    int nrep;
+    int ntot;
+    int ctot;
+    const int *need;
+    Ctrl *ctrl;
+    Thermo *th;
+};
+
+// Launchers (defined in md_kernels_*.cu, one translation unit per precision).
+template <typename R> cudaError_t launch_step(const StepArgs<R> &a, int tp, int block, int ntiles,
+                                              cudaStream_t s);
+template <typename R> cudaError_t launch_rebuild(const RebuildArgs<R> &a, cudaStream_t s);
+template <typename R> cudaError_t launch_rebuild_timed(const RebuildArgs<R> &a, cudaStream_t s,
+                                                       cudaEvent_t e0, cudaEvent_t e1);
+cudaError_t launch_arm(const Ctrl *ctrl, cudaGraphConditionalHandle h, cudaStream_t s);

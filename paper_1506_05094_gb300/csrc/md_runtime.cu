@@ -1,0 +1,1435 @@
+// md_runtime.cu -- host runtime behind the C ABI of include/md.h: device memory, replica layout,
+// state upload / download in user order, the step scheduler (CUDA graphs with IF nodes around
+// the rebuild, or plain launches), overflow recovery, checkpoints, logging and profiling.
+#include "md.h"
+#include "md_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+namespace {
+
+const int kMaxTypes = MD_MAX_TYPES;
+
+struct Buffers {
+    void *pos[2] = {nullptr, nullptr};
+    double *xd = nullptr, *yd = nullptr, *zd = nullptr;
+    void *vel = nullptr;
+    int4 *img = nullptr;
+    int *id = nullptr;
+    void *pos_build = nullptr;
+    void *tpos = nullptr, *tkey = nullptr;
+    double *txd = nullptr, *tyd = nullptr, *tzd = nullptr;
+    void *tvel = nullptr;
+    int4 *timg = nullptr;
+    int *tid = nullptr;
+    int *cell_of = nullptr, *rank = nullptr, *perm = nullptr;
+    int *cell_start = nullptr, *count = nullptr, *crep = nullptr, *prep = nullptr;
+    int *nbl = nullptr, *nnb = nullptr;
+    SysDesc *sys = nullptr;
+    PairTab *tab = nullptr;
+    Thermo *th = nullptr;
+    Ctrl *ctrl = nullptr;
+    int *moved = nullptr, *need = nullptr;
+    unsigned *ticket = nullptr;
+    double *partial = nullptr;
+    int *tile_rep = nullptr;
+    double *log = nullptr;
+    void *f_out = nullptr, *w_out = nullptr;
+};
+
+}  // namespace
+
+struct md_sim {
+    int R = 0, nt = 0, precision = MD_MIXED, cutoff = MD_SHIFTED_POTENTIAL;
+    int ntot = 0, ctot = 0, ntiles = 0;
+    std::vector<int> n, off;
+    std::vector<double> L;
+    std::vector<md_pair> params;
+    std::vector<PairTab> tab;
+    std::vector<SysDesc> sys;
+    double mass[kMaxTypes], inv_mass[kMaxTypes];
+    double skin = 0.3, rc_max = 0.0;
+    int integrator = MD_NVE_LEAPFROG;
+    double dt = 0.005, T0 = 1.0, tau = 0.2;
+    int tp = 1, block = 128, reach = 2;
+    int graph_block = 100;
+    int nmax = 0;
+    int log_cap = 0;
+    std::vector<char> loaded;
+    size_t r4 = 16;   // bytes of one Real4
+    Buffers b;
+    cudaStream_t stream = nullptr, cap_stream = nullptr, body_stream = nullptr;
+    bool own_stream = false;
+    Ctrl *h_ctrl = nullptr;  // pinned
+    long long h_step = 0;    // completed steps (host view)
+    cudaGraph_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    int graph_len[2] = {0, 0};
+    int sticky = MD_OK;
+    long long overflows = 0;
+    int device = 0;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+};
+
+namespace {
+
+#define CK(call)                                                                                \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess) {                                                                \
+            std::fprintf(stderr, "md: CUDA error %s at %s:%d: %s\n", cudaGetErrorName(e_),      \
+                         __FILE__, __LINE__, cudaGetErrorString(e_));                           \
+            return fail(s, MD_ECUDA);                                                           \
+        }                                                                                       \
+    } while (0)
+
+int fail(md_sim *s, int code) {
+    if (s && (code == MD_ECUDA || code == MD_EUNSTABLE || code == MD_ETIMEOUT) &&
+        s->sticky == MD_OK)
+        s->sticky = code;
+    return code;
+}
+
+template <typename T> int dalloc(md_sim *s, T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return MD_ENOMEM;
+    }
+    return MD_OK;
+}
+int dallocb(md_sim *s, void **p, size_t bytes) {
+    (void)s;
+    *p = nullptr;
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 1);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return MD_ENOMEM;
+    }
+    return MD_OK;
+}
+template <typename T> void dfree(T *&p) {
+    if (p) cudaFree((void *)p);
+    p = nullptr;
+}
+
+void destroy_graphs(md_sim *s) {
+    for (int k = 0; k < 2; ++k) {
+        if (s->exec[k]) cudaGraphExecDestroy(s->exec[k]);
+        if (s->graph[k]) cudaGraphDestroy(s->graph[k]);
+        s->exec[k] = nullptr;
+        s->graph[k] = nullptr;
+        s->graph_len[k] = 0;
+    }
+}
+
+bool is_pow2_tp(int tp) {
+    return tp == 1 || tp == 2 || tp == 4 || tp == 8 || tp == 16 || tp == 32;
+}
+
+// Cells per box edge for a stencil reach: edge >= (rc_max + skin) / reach with a 1e-4 margin
+// so that FP32 rounding of the cell coordinate never breaks the stencil guarantee.
+int cells_per_edge(double L, double rc_max, double skin, int reach) {
+    const double min_edge = (rc_max + skin) / reach * (1.0 + 1e-4);
+    int nc = (int)std::floor(L / min_edge);
+    return nc < 1 ? 1 : nc;
+}
+
+// (Re)compute cells and tiles for the current tuning; (re)allocate what depends on them.
+int configure_layout(md_sim *s, bool realloc_cells) {
+    int ctot = 0, ntiles = 0;
+    const int P = s->block / s->tp;
+    for (int r = 0; r < s->R; ++r) {
+        SysDesc &d = s->sys[r];
+        d.nc = cells_per_edge(s->L[r], s->rc_max, s->skin, s->reach);
+        d.reach = s->reach;
+        d.span = std::min(2 * s->reach + 1, d.nc);
+        d.cell_scale = (float)(d.nc / s->L[r]);
+        d.cell_off = ctot;
+        ctot += d.nc * d.nc * d.nc;
+        d.tile_off = ntiles;
+        d.ntiles = (d.n + P - 1) / P;
+        ntiles += d.ntiles;
+    }
+    if (realloc_cells || ctot != s->ctot) {
+        dfree(s->b.cell_start);
+        dfree(s->b.count);
+        dfree(s->b.crep);
+        s->ctot = ctot;
+        if (dalloc(s, &s->b.cell_start, (size_t)ctot + 1) || dalloc(s, &s->b.count, ctot) ||
+            dalloc(s, &s->b.crep, ctot))
+            return MD_ENOMEM;
+        std::vector<int> cs((size_t)ctot + 1), cr(ctot);
+        for (int r = 0; r < s->R; ++r) {
+            const SysDesc &d = s->sys[r];
+            const int C = d.nc * d.nc * d.nc;
+            for (int c = 0; c < C; ++c) {
+                cs[d.cell_off + c] = d.off;   // all cells empty until the first build
+                cr[d.cell_off + c] = r;
+            }
+        }
+        cs[ctot] = s->ntot;
+        if (cudaMemcpy(s->b.cell_start, cs.data(), cs.size() * sizeof(int),
+                       cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(s->b.crep, cr.data(), cr.size() * sizeof(int), cudaMemcpyHostToDevice) !=
+                cudaSuccess ||
+            cudaMemset(s->b.count, 0, sizeof(int) * (size_t)std::max(ctot, 1)) != cudaSuccess)
+            return fail(s, MD_ECUDA);
+    }
+    if (ntiles != s->ntiles || s->b.tile_rep == nullptr) {
+        dfree(s->b.tile_rep);
+        dfree(s->b.partial);
+        s->ntiles = ntiles;
+        if (dalloc(s, &s->b.tile_rep, ntiles) ||
+            dalloc(s, &s->b.partial, (size_t)ntiles * MD_NRED))
+            return MD_ENOMEM;
+    }
+    std::vector<int> tr(ntiles);
+    for (int r = 0; r < s->R; ++r)
+        for (int t = 0; t < s->sys[r].ntiles; ++t) tr[s->sys[r].tile_off + t] = r;
+    if (cudaMemcpy(s->b.tile_rep, tr.data(), tr.size() * sizeof(int), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(s->b.sys, s->sys.data(), s->sys.size() * sizeof(SysDesc),
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(s, MD_ECUDA);
+    return MD_OK;
+}
+
+int alloc_nbl(md_sim *s) {
+    dfree(s->b.nbl);
+    return dalloc(s, &s->b.nbl, (size_t)s->ntot * (size_t)s->nmax);
+}
+
+// Force a full rebuild of every replica before the next step (device flags, stream-ordered).
+int request_rebuild_all(md_sim *s) {
+    std::vector<int> ones(s->R, 1);
+    if (cudaMemcpyAsync(s->b.need, ones.data(), sizeof(int) * s->R, cudaMemcpyHostToDevice,
+                        s->stream) != cudaSuccess)
+        return fail(s, MD_ECUDA);
+    const int one = 1;
+    if (cudaMemcpyAsync(&s->b.ctrl->need_any, &one, sizeof(int), cudaMemcpyHostToDevice,
+                        s->stream) != cudaSuccess ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess)
+        return fail(s, MD_ECUDA);
+    return MD_OK;
+}
+
+template <typename R> StepArgs<R> step_args(md_sim *s, int parity, int force_only) {
+    typedef typename V4T<R>::t V4;
+    StepArgs<R> a;
+    std::memset(&a, 0, sizeof(a));
+    a.pos_in = (const V4 *)s->b.pos[parity];
+    a.pos_out = (V4 *)s->b.pos[parity ^ 1];
+    a.xd = s->b.xd; a.yd = s->b.yd; a.zd = s->b.zd;
+    a.vel = (V4 *)s->b.vel;
+    a.img = s->b.img;
+    a.pos_build = (const V4 *)s->b.pos_build;
+    a.nbl = s->b.nbl;
+    a.nnb = s->b.nnb;
+    a.ncap = s->ntot;
+    a.tile_rep = s->b.tile_rep;
+    a.sys = s->b.sys;
+    a.tab = s->b.tab;
+    a.ntypes = s->nt;
+    a.nrep = s->R;
+    for (int t = 0; t < kMaxTypes; ++t) {
+        a.inv_mass[t] = s->inv_mass[t];
+        a.mass[t] = s->mass[t];
+    }
+    a.th = s->b.th;
+    a.ctrl = s->b.ctrl;
+    a.moved = s->b.moved;
+    a.need = s->b.need;
+    a.rep_ticket = s->b.ticket;
+    a.partial = s->b.partial;
+    a.log = s->b.log;
+    a.log_cap = s->log_cap;
+    a.integrator = s->integrator;
+    a.dt = s->dt;
+    a.T0 = s->T0;
+    a.inv_tau2 = (s->integrator == MD_NVT_NOSE_HOOVER) ? 1.0 / (s->tau * s->tau) : 0.0;
+    a.half_skin2 = (R)(0.25 * s->skin * s->skin);
+    a.force_only = force_only;
+    a.f_out = (V4 *)s->b.f_out;
+    a.w_out = (R *)s->b.w_out;
+    a.has_next = 0;
+    return a;
+}
+
+template <typename R> RebuildArgs<R> rebuild_args(md_sim *s, int parity, const void *key) {
+    typedef typename V4T<R>::t V4;
+    RebuildArgs<R> a;
+    std::memset(&a, 0, sizeof(a));
+    a.pos = (V4 *)s->b.pos[parity];
+    a.key = key ? (const V4 *)key : (const V4 *)s->b.pos[parity];
+    a.key_is_pos = key ? 0 : 1;
+    a.xd = s->b.xd; a.yd = s->b.yd; a.zd = s->b.zd;
+    a.vel = (V4 *)s->b.vel;
+    a.img = s->b.img;
+    a.id = s->b.id;
+    a.pos_build = (V4 *)s->b.pos_build;
+    a.tpos = (V4 *)s->b.tpos;
+    a.tkey = (V4 *)s->b.tkey;
+    a.txd = s->b.txd; a.tyd = s->b.tyd; a.tzd = s->b.tzd;
+    a.tvel = (V4 *)s->b.tvel;
+    a.timg = s->b.timg;
+    a.tid = s->b.tid;
+    a.cell_of = s->b.cell_of;
+    a.rank = s->b.rank;
+    a.perm = s->b.perm;
+    a.cell_start = s->b.cell_start;
+    a.count = s->b.count;
+    a.prep = s->b.prep;
+    a.crep = s->b.crep;
+    a.nbl = s->b.nbl;
+    a.nnb = s->b.nnb;
+    a.ncap = s->ntot;
+    a.nmax = s->nmax;
+    a.sys = s->b.sys;
+    a.tab = s->b.tab;
+    a.ntypes = s->nt;
+    a.nrep = s->R;
+    a.ntot = s->ntot;
+    a.ctot = s->ctot;
+    a.need = s->b.need;
+    a.ctrl = s->b.ctrl;
+    a.th = s->b.th;
+    return a;
+}
+
+cudaError_t do_rebuild(md_sim *s, int parity, cudaStream_t st, const void *key = nullptr) {
+    if (s->precision == MD_FP64) return launch_rebuild<double>(rebuild_args<double>(s, parity, key), st);
+    return launch_rebuild<float>(rebuild_args<float>(s, parity, key), st);
+}
+
+cudaError_t do_step(md_sim *s, int parity, cudaStream_t st, int force_only,
+                    cudaGraphConditionalHandle next = 0, int has_next = 0) {
+    if (s->precision == MD_FP64) {
+        StepArgs<double> a = step_args<double>(s, parity, force_only);
+        a.next_handle = next;
+        a.has_next = has_next;
+        return launch_step<double>(a, s->tp, s->block, s->ntiles, st);
+    }
+    StepArgs<float> a = step_args<float>(s, parity, force_only);
+    a.next_handle = next;
+    a.has_next = has_next;
+    return launch_step<float>(a, s->tp, s->block, s->ntiles, st);
+}
+
+// Capture graph_block steps starting at step parity p: [IF need_any {rebuild}] -> step, repeated.
+int build_graph(md_sim *s, int p) {
+    const int B = s->graph_block;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return fail(s, MD_ECUDA);
+    cudaStreamCaptureStatus st;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    std::vector<cudaGraphConditionalHandle> h(B);
+    bool ok = cudaStreamGetCaptureInfo(s->cap_stream, &st, nullptr, &g, &deps, nullptr, &ndeps) ==
+              cudaSuccess;
+    for (int k = 0; ok && k < B; ++k)
+        ok = cudaGraphConditionalHandleCreate(&h[k], g, 0, cudaGraphCondAssignDefault) ==
+             cudaSuccess;
+    ok = ok && launch_arm(s->b.ctrl, h[0], s->cap_stream) == cudaSuccess;
+    for (int k = 0; ok && k < B; ++k) {
+        const int q = (p + k) & 1;
+        ok = cudaStreamGetCaptureInfo(s->cap_stream, &st, nullptr, &g, &deps, nullptr, &ndeps) ==
+             cudaSuccess;
+        if (!ok) break;
+        cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+        cp.conditional.handle = h[k];
+        cp.conditional.type = cudaGraphCondTypeIf;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node;
+        ok = cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &cp) == cudaSuccess;
+        if (!ok) break;
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        ok = cudaStreamUpdateCaptureDependencies(s->cap_stream, &node, nullptr, 1,
+                                                 cudaStreamSetCaptureDependencies) == cudaSuccess;
+        ok = ok && cudaStreamBeginCaptureToGraph(s->body_stream, body, nullptr, nullptr, 0,
+                                                 cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (!ok) break;
+        cudaError_t e1 = do_rebuild(s, q, s->body_stream);
+        cudaGraph_t body_out = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(s->body_stream, &body_out);
+        ok = e1 == cudaSuccess && e2 == cudaSuccess;
+        ok = ok && do_step(s, q, s->cap_stream, 0, k + 1 < B ? h[k + 1] : 0, k + 1 < B) ==
+                       cudaSuccess;
+    }
+    cudaGraph_t out = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s->cap_stream, &out);
+    if (!ok || e != cudaSuccess || out == nullptr) {
+        if (out) cudaGraphDestroy(out);
+        cudaGetLastError();
+        return fail(s, MD_ECUDA);
+    }
+    cudaGraphExec_t ex = nullptr;
+    if (cudaGraphInstantiate(&ex, out, 0) != cudaSuccess) {
+        cudaGraphDestroy(out);
+        return fail(s, MD_ECUDA);
+    }
+    s->graph[p] = out;
+    s->exec[p] = ex;
+    s->graph_len[p] = B;
+    return MD_OK;
+}
+
+int read_ctrl(md_sim *s) {
+    if (cudaMemcpyAsync(s->h_ctrl, s->b.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess)
+        return fail(s, MD_ECUDA);
+    return MD_OK;
+}
+
+// After an overflow: double n_max (at least to the largest count seen), rebuild everything.
+int recover_overflow(md_sim *s) {
+    const int seen = s->h_ctrl->max_count;
+    int nm = std::max(2 * s->nmax, seen + seen / 4 + 8);
+    s->nmax = nm;
+    destroy_graphs(s);
+    if (alloc_nbl(s)) return MD_ENOMEM;
+    Ctrl c = *s->h_ctrl;
+    c.overflow = 0;
+    c.halt = 0;
+    c.max_count = 0;
+    c.global_ticket = 0;
+    if (cudaMemcpyAsync(s->b.ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, s->stream) !=
+            cudaSuccess ||
+        cudaMemsetAsync(s->b.ticket, 0, sizeof(unsigned) * s->R, s->stream) != cudaSuccess)
+        return fail(s, MD_ECUDA);
+    s->overflows++;
+    return request_rebuild_all(s);
+}
+
+// Run a plain rebuild pass now (if flagged) and recover from overflow until the list fits.
+int ensure_list(md_sim *s) {
+    for (int tries = 0; tries < 16; ++tries) {
+        if (do_rebuild(s, (int)(s->h_step & 1), s->stream) != cudaSuccess) return fail(s, MD_ECUDA);
+        int rc = read_ctrl(s);
+        if (rc) return rc;
+        if (s->h_ctrl->unstable) return fail(s, MD_EUNSTABLE);
+        if (!s->h_ctrl->overflow) return MD_OK;
+        if ((rc = recover_overflow(s))) return rc;
+    }
+    return fail(s, MD_ECUDA);
+}
+
+int check_replica(md_sim *s, int r) {
+    if (!s) return MD_EINVAL;
+    if (r < 0 || r >= s->R) return MD_EINVAL;
+    return MD_OK;
+}
+
+template <typename R> void pack_v4(std::vector<unsigned char> &dst, size_t k, double x, double y,
+                                   double z, double w) {
+    R v[4] = {(R)x, (R)y, (R)z, (R)w};
+    std::memcpy(dst.data() + k * sizeof(v), v, sizeof(v));
+}
+
+// type word stored in .w of a position mirror
+void pack_pos(const md_sim *s, std::vector<unsigned char> &dst, size_t k, double x, double y,
+              double z, int type) {
+    if (s->precision == MD_FP64) {
+        double v[4] = {x, y, z, 0.0};
+        long long t = type;
+        std::memcpy(&v[3], &t, sizeof(double));
+        std::memcpy(dst.data() + k * 32, v, 32);
+    } else {
+        float v[4] = {(float)x, (float)y, (float)z, 0.0f};
+        std::memcpy(&v[3], &type, sizeof(float));
+        std::memcpy(dst.data() + k * 16, v, 16);
+    }
+}
+
+void unpack_v4(const md_sim *s, const std::vector<unsigned char> &src, size_t k, double *out3) {
+    if (s->precision == MD_FP64) {
+        double v[4];
+        std::memcpy(v, src.data() + k * 32, 32);
+        out3[0] = v[0]; out3[1] = v[1]; out3[2] = v[2];
+    } else {
+        float v[4];
+        std::memcpy(v, src.data() + k * 16, 16);
+        out3[0] = v[0]; out3[1] = v[1]; out3[2] = v[2];
+    }
+}
+
+}  // namespace
+
+// ================================================================================================
+// C ABI
+// ================================================================================================
+extern "C" {
+
+const char *md_strerror(int status) {
+    switch (status) {
+    case MD_OK: return "ok";
+    case MD_EINVAL: return "invalid argument or violated precondition";
+    case MD_ENOMEM: return "out of memory";
+    case MD_ECUDA: return "CUDA runtime error";
+    case MD_EUNSTABLE: return "unstable: non-finite or runaway displacement";
+    case MD_ETIMEOUT: return "bounded device wait timed out";
+    case MD_ESTATE: return "call out of order (state not loaded)";
+    default: return "unknown md status";
+    }
+}
+
+void md_destroy(md_sim *s) {
+    if (!s) return;
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    destroy_graphs(s);
+    Buffers &b = s->b;
+    void **ptrs[] = {&b.pos[0], &b.pos[1], (void **)&b.xd, (void **)&b.yd, (void **)&b.zd, &b.vel,
+                     (void **)&b.img, (void **)&b.id, &b.pos_build, &b.tpos, &b.tkey,
+                     (void **)&b.txd, (void **)&b.tyd, (void **)&b.tzd, &b.tvel, (void **)&b.timg,
+                     (void **)&b.tid, (void **)&b.cell_of, (void **)&b.rank, (void **)&b.perm,
+                     (void **)&b.cell_start, (void **)&b.count, (void **)&b.crep,
+                     (void **)&b.prep, (void **)&b.nbl, (void **)&b.nnb, (void **)&b.sys,
+                     (void **)&b.tab, (void **)&b.th, (void **)&b.ctrl, (void **)&b.moved,
+                     (void **)&b.need, (void **)&b.ticket, (void **)&b.partial,
+                     (void **)&b.tile_rep, (void **)&b.log, &b.f_out, &b.w_out};
+    for (void **p : ptrs) {
+        if (*p) cudaFree(*p);
+        *p = nullptr;
+    }
+    if (s->h_ctrl) cudaFreeHost(s->h_ctrl);
+    for (cudaEvent_t &e : s->ev)
+        if (e) cudaEventDestroy(e);
+    if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+    if (s->body_stream) cudaStreamDestroy(s->body_stream);
+    if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+}
+
+int md_create(md_sim **out, int n_replicas, const int *n_particles, const double *box,
+              int n_types, const md_pair *params, const double *mass, double skin,
+              int cutoff_method, int precision) {
+    if (!out) return MD_EINVAL;
+    *out = nullptr;
+    if (n_replicas < 1 || !n_particles || !box || !params || n_types < 1 ||
+        n_types > kMaxTypes || !(skin > 0.0) || !std::isfinite(skin) ||
+        cutoff_method != MD_SHIFTED_POTENTIAL || (precision != MD_MIXED && precision != MD_FP64))
+        return MD_EINVAL;
+    double rc_max = 0.0;
+    for (int a = 0; a < n_types; ++a)
+        for (int c = 0; c < n_types; ++c) {
+            const md_pair &p = params[a * n_types + c], &q = params[c * n_types + a];
+            if (!(p.eps >= 0.0) || !(p.sigma > 0.0) || !(p.rc > 0.0) || !std::isfinite(p.eps) ||
+                !std::isfinite(p.sigma) || !std::isfinite(p.rc))
+                return MD_EINVAL;
+            if (p.eps != q.eps || p.sigma != q.sigma || p.rc != q.rc) return MD_EINVAL;
+            rc_max = std::max(rc_max, p.rc);
+        }
+    if (mass)
+        for (int t = 0; t < n_types; ++t)
+            if (!(mass[t] > 0.0) || !std::isfinite(mass[t])) return MD_EINVAL;
+    long long ntot = 0;
+    for (int r = 0; r < n_replicas; ++r) {
+        if (n_particles[r] < 2) return MD_EINVAL;
+        if (!(box[r] > 2.0 * (rc_max + skin)) || !std::isfinite(box[r])) return MD_EINVAL;
+        ntot += n_particles[r];
+    }
+    if (ntot > (1LL << 30)) return MD_EINVAL;
+
+    md_sim *s = new (std::nothrow) md_sim();
+    if (!s) return MD_ENOMEM;
+    cudaGetDevice(&s->device);
+    s->R = n_replicas;
+    s->nt = n_types;
+    s->precision = precision;
+    s->cutoff = cutoff_method;
+    s->skin = skin;
+    s->rc_max = rc_max;
+    s->r4 = precision == MD_FP64 ? 32 : 16;
+    s->ntot = (int)ntot;
+    s->n.assign(n_particles, n_particles + n_replicas);
+    s->L.assign(box, box + n_replicas);
+    s->params.assign(params, params + n_types * n_types);
+    s->loaded.assign(n_replicas, 0);
+    for (int t = 0; t < kMaxTypes; ++t) {
+        s->mass[t] = (mass && t < n_types) ? mass[t] : 1.0;
+        s->inv_mass[t] = 1.0 / s->mass[t];
+    }
+    // pair table: u = c12 r^-12 - c6 r^-6 - u(rc), F = r^-2 (12 c12 r^-12 - 6 c6 r^-6) r_ij
+    s->tab.resize(MD_MAX_PAIRS);
+    std::memset(s->tab.data(), 0, sizeof(PairTab) * MD_MAX_PAIRS);
+    for (int p = 0; p < n_types * n_types; ++p) {
+        const md_pair &q = params[p];
+        const double s6 = std::pow(q.sigma, 6.0), c12 = 4.0 * q.eps * s6 * s6, c6 = 4.0 * q.eps * s6;
+        const double rc6 = std::pow(q.rc, 6.0);
+        const double ush = c12 / (rc6 * rc6) - c6 / rc6;
+        const double thr2 = (q.rc + skin) * (q.rc + skin);
+        PairTab &t = s->tab[p];
+        t.rc2d = q.rc * q.rc; t.c12d = c12; t.c6d = c6; t.ushiftd = ush;
+        t.a12d = 12.0 * c12; t.a6d = 6.0 * c6; t.thr2d = thr2;
+        t.rc2 = (float)t.rc2d; t.c12 = (float)c12; t.c6 = (float)c6; t.ushift = (float)ush;
+        t.a12 = (float)t.a12d; t.a6 = (float)t.a6d; t.thr2 = (float)thr2;
+    }
+    // replicas
+    s->off.resize(n_replicas);
+    s->sys.resize(n_replicas);
+    int off = 0;
+    double nmax_est = 0.0;
+    int n_big = 0;
+    for (int r = 0; r < n_replicas; ++r) {
+        SysDesc &d = s->sys[r];
+        std::memset(&d, 0, sizeof(d));
+        d.off = off;
+        d.n = n_particles[r];
+        d.L = box[r];
+        d.invL = 1.0 / box[r];
+        d.Lf = (float)box[r];
+        d.invLf = (float)(1.0 / box[r]);
+        d.K0 = 0.5 * (3.0 * d.n - 3.0) * s->T0;
+        s->off[r] = off;
+        off += d.n;
+        const double rho = d.n / (box[r] * box[r] * box[r]);
+        const double rl = rc_max + skin;
+        nmax_est = std::max(nmax_est, rho * 4.18879020478639 * rl * rl * rl);
+        n_big = std::max(n_big, d.n);
+    }
+    // Sec. 4: fixed-capacity list; start with headroom and grow x2 on overflow
+    int nmax = (int)std::ceil(nmax_est * 1.35) + 24;
+    nmax = std::min(nmax, n_big - 1);
+    s->nmax = std::max(nmax, 1);
+    s->tp = 1;
+    s->block = 128;
+    s->reach = 2;
+
+    int rc = MD_OK;
+    const size_t N = (size_t)ntot, R4 = s->r4;
+    Buffers &b = s->b;
+    rc |= dallocb(s, &b.pos[0], N * R4);
+    rc |= dallocb(s, &b.pos[1], N * R4);
+    rc |= dalloc(s, &b.xd, N); rc |= dalloc(s, &b.yd, N); rc |= dalloc(s, &b.zd, N);
+    rc |= dallocb(s, &b.vel, N * R4);
+    rc |= dalloc(s, &b.img, N);
+    rc |= dalloc(s, &b.id, N);
+    rc |= dallocb(s, &b.pos_build, N * R4);
+    rc |= dallocb(s, &b.tpos, N * R4);
+    rc |= dallocb(s, &b.tkey, N * R4);
+    rc |= dalloc(s, &b.txd, N); rc |= dalloc(s, &b.tyd, N); rc |= dalloc(s, &b.tzd, N);
+    rc |= dallocb(s, &b.tvel, N * R4);
+    rc |= dalloc(s, &b.timg, N);
+    rc |= dalloc(s, &b.tid, N);
+    rc |= dalloc(s, &b.cell_of, N); rc |= dalloc(s, &b.rank, N); rc |= dalloc(s, &b.perm, N);
+    rc |= dalloc(s, &b.prep, N);
+    rc |= dalloc(s, &b.nnb, N);
+    rc |= dalloc(s, &b.sys, n_replicas);
+    rc |= dalloc(s, &b.tab, MD_MAX_PAIRS);
+    rc |= dalloc(s, &b.th, n_replicas);
+    rc |= dalloc(s, &b.ctrl, 1);
+    rc |= dalloc(s, &b.moved, n_replicas);
+    rc |= dalloc(s, &b.need, n_replicas);
+    rc |= dalloc(s, &b.ticket, n_replicas);
+    rc |= dallocb(s, &b.f_out, N * R4);
+    rc |= dallocb(s, &b.w_out, N * (R4 / 4));
+    if (rc) { md_destroy(s); return MD_ENOMEM; }
+    if (alloc_nbl(s)) { md_destroy(s); return MD_ENOMEM; }
+    if (cudaMallocHost((void **)&s->h_ctrl, sizeof(Ctrl)) != cudaSuccess) {
+        s->h_ctrl = nullptr;
+        md_destroy(s);
+        return MD_ENOMEM;
+    }
+    std::vector<int> prep(N);
+    for (int r = 0; r < n_replicas; ++r)
+        for (int k = 0; k < s->n[r]; ++k) prep[s->off[r] + k] = r;
+    bool ok = cudaMemcpy(b.prep, prep.data(), N * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemcpy(b.tab, s->tab.data(), sizeof(PairTab) * MD_MAX_PAIRS,
+                          cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemset(b.th, 0, sizeof(Thermo) * n_replicas) == cudaSuccess;
+    ok = ok && cudaMemset(b.ctrl, 0, sizeof(Ctrl)) == cudaSuccess;
+    ok = ok && cudaMemset(b.moved, 0, sizeof(int) * n_replicas) == cudaSuccess;
+    ok = ok && cudaMemset(b.need, 0, sizeof(int) * n_replicas) == cudaSuccess;
+    ok = ok && cudaMemset(b.ticket, 0, sizeof(unsigned) * n_replicas) == cudaSuccess;
+    ok = ok && cudaMemset(b.nnb, 0, sizeof(int) * N) == cudaSuccess;
+    ok = ok && cudaMemset(b.img, 0, sizeof(int4) * N) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) == cudaSuccess;
+    s->own_stream = ok;
+    ok = ok && cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithFlags(&s->body_stream, cudaStreamNonBlocking) == cudaSuccess;
+    for (int k = 0; ok && k < 3; ++k) ok = cudaEventCreate(&s->ev[k]) == cudaSuccess;
+    if (!ok) { md_destroy(s); return MD_ECUDA; }
+    rc = configure_layout(s, true);
+    if (rc) { md_destroy(s); return rc == MD_ENOMEM ? MD_ENOMEM : MD_ECUDA; }
+    *out = s;
+    return MD_OK;
+}
+
+int md_set_integrator(md_sim *s, int kind, double dt, double T, double tau) {
+    if (!s) return MD_EINVAL;
+    if (s->sticky) return s->sticky;
+    if (kind != MD_NVE_LEAPFROG && kind != MD_NVT_NOSE_HOOVER) return MD_EINVAL;
+    if (!(dt > 0.0) || !std::isfinite(dt)) return MD_EINVAL;
+    if (kind == MD_NVT_NOSE_HOOVER && (!(T > 0.0) || !(tau > 0.0) || !std::isfinite(T) ||
+                                       !std::isfinite(tau)))
+        return MD_EINVAL;
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(s, MD_ECUDA);
+    s->integrator = kind;
+    s->dt = dt;
+    s->T0 = kind == MD_NVT_NOSE_HOOVER ? T : (std::isfinite(T) && T > 0 ? T : 1.0);
+    s->tau = kind == MD_NVT_NOSE_HOOVER ? tau : 0.2;
+    for (auto &d : s->sys) d.K0 = 0.5 * (3.0 * d.n - 3.0) * s->T0;
+    if (cudaMemcpy(s->b.sys, s->sys.data(), s->sys.size() * sizeof(SysDesc),
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(s, MD_ECUDA);
+    destroy_graphs(s);
+    return MD_OK;
+}
+
+int md_set_stream(md_sim *s, void *cuda_stream) {
+    if (!s) return MD_EINVAL;
+    if (s->sticky) return s->sticky;
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(s, MD_ECUDA);
+    if (s->own_stream) cudaStreamDestroy(s->stream);
+    s->own_stream = false;
+    s->stream = (cudaStream_t)cuda_stream;
+    return MD_OK;
+}
+
+int md_set_state(md_sim *s, int r, const double *pos, const int *type, const double *vel,
+                 const int *image) {
+    int rc = check_replica(s, r);
+    if (rc) return rc;
+    if (s->sticky) return s->sticky;
+    if (!pos || !type || !vel) return MD_EINVAL;
+    const int n = s->n[r];
+    const double L = s->L[r];
+    for (int k = 0; k < n; ++k) {
+        if (type[k] < 0 || type[k] >= s->nt) return MD_EINVAL;
+        for (int c = 0; c < 3; ++c)
+            if (!std::isfinite(pos[3 * k + c]) || !std::isfinite(vel[3 * k + c])) return MD_EINVAL;
+    }
+    std::vector<double> x(n), y(n), z(n);
+    std::vector<int4> img(n);
+    std::vector<int> ids(n);
+    std::vector<unsigned char> mirror((size_t)n * s->r4), vv((size_t)n * s->r4);
+    double K = 0.0;
+    for (int k = 0; k < n; ++k) {
+        double w3[3];
+        int im3[3];
+        for (int c = 0; c < 3; ++c) {
+            double v = pos[3 * k + c];
+            double f = std::floor(v / L);
+            v -= f * L;
+            if (v >= L) { v -= L; f += 1.0; }
+            if (v < 0.0) { v += L; f -= 1.0; }
+            if (v >= L) v = 0.0;   // -tiny + L rounded up to L
+            w3[c] = v;
+            im3[c] = (int)f + (image ? image[3 * k + c] : 0);
+        }
+        x[k] = w3[0]; y[k] = w3[1]; z[k] = w3[2];
+        img[k] = make_int4(im3[0], im3[1], im3[2], 0);
+        ids[k] = k;
+        pack_pos(s, mirror, k, w3[0], w3[1], w3[2], type[k]);
+        double vs[3];
+        if (s->precision == MD_FP64) {
+            pack_v4<double>(vv, k, vel[3 * k], vel[3 * k + 1], vel[3 * k + 2], 0.0);
+            vs[0] = vel[3 * k]; vs[1] = vel[3 * k + 1]; vs[2] = vel[3 * k + 2];
+        } else {
+            pack_v4<float>(vv, k, vel[3 * k], vel[3 * k + 1], vel[3 * k + 2], 0.0);
+            vs[0] = (float)vel[3 * k]; vs[1] = (float)vel[3 * k + 1]; vs[2] = (float)vel[3 * k + 2];
+        }
+        K += 0.5 * s->mass[type[k]] * (vs[0] * vs[0] + vs[1] * vs[1] + vs[2] * vs[2]);
+    }
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(s, MD_ECUDA);
+    const int o = s->off[r];
+    const int cur = (int)(s->h_step & 1);
+    const size_t R4 = s->r4;
+    Buffers &b = s->b;
+    Thermo th;
+    std::memset(&th, 0, sizeof(th));
+    th.K_prev = K;
+    const int one = 1, zero = 0;
+    bool ok = true;
+    ok = ok && cudaMemcpy((char *)b.pos[cur] + o * R4, mirror.data(), n * R4, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemcpy((char *)b.pos_build + o * R4, mirror.data(), n * R4, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemcpy(b.xd + o, x.data(), n * 8, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemcpy(b.yd + o, y.data(), n * 8, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemcpy(b.zd + o, z.data(), n * 8, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemcpy((char *)b.vel + o * R4, vv.data(), n * R4, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemcpy(b.img + o, img.data(), n * sizeof(int4), cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemcpy(b.id + o, ids.data(), n * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemset(b.nnb + o, 0, n * sizeof(int)) == cudaSuccess;
+    ok = ok && cudaMemcpy(b.th + r, &th, sizeof(th), cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemcpy(b.need + r, &one, sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemcpy(b.moved + r, &zero, sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemcpy(&b.ctrl->need_any, &one, sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) return fail(s, MD_ECUDA);
+    s->loaded[r] = 1;
+    return MD_OK;
+}
+
+int md_step(md_sim *s, long long n_steps) {
+    if (!s || n_steps < 0) return MD_EINVAL;
+    if (s->sticky) return s->sticky;
+    for (char c : s->loaded)
+        if (!c) return MD_ESTATE;
+    long long remaining = n_steps;
+    int guard = 0;
+    while (remaining > 0) {
+        const long long start = s->h_step;
+        while (remaining > 0) {
+            const int p = (int)(s->h_step & 1);
+            if (s->graph_block > 0 && remaining >= s->graph_block) {
+                if (s->exec[p] == nullptr || s->graph_len[p] != s->graph_block) {
+                    if (s->exec[p]) {
+                        cudaGraphExecDestroy(s->exec[p]);
+                        cudaGraphDestroy(s->graph[p]);
+                        s->exec[p] = nullptr;
+                        s->graph[p] = nullptr;
+                    }
+                    int rc = build_graph(s, p);
+                    if (rc) return rc;
+                }
+                if (cudaGraphLaunch(s->exec[p], s->stream) != cudaSuccess) return fail(s, MD_ECUDA);
+                s->h_step += s->graph_block;
+                remaining -= s->graph_block;
+            } else {
+                if (do_rebuild(s, p, s->stream) != cudaSuccess ||
+                    do_step(s, p, s->stream, 0) != cudaSuccess)
+                    return fail(s, MD_ECUDA);
+                s->h_step += 1;
+                remaining -= 1;
+            }
+        }
+        int rc = read_ctrl(s);
+        if (rc) return rc;
+        if (s->h_ctrl->unstable) return fail(s, MD_EUNSTABLE);
+        if (s->h_ctrl->overflow) {
+            // steps after the overflowing build were skipped on the device; redo them
+            const long long done = s->h_ctrl->step;
+            remaining += s->h_step - done;
+            s->h_step = done;
+            if (++guard > 16) return fail(s, MD_ECUDA);
+            if ((rc = recover_overflow(s))) return rc;
+            (void)start;
+            continue;
+        }
+        if (s->h_ctrl->step != s->h_step) return fail(s, MD_ECUDA);
+    }
+    return MD_OK;
+}
+
+int md_sync(md_sim *s) {
+    if (!s) return MD_EINVAL;
+    if (s->sticky) return s->sticky;
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(s, MD_ECUDA);
+    return MD_OK;
+}
+
+int md_get_state(md_sim *s, int r, double *pos, int *image, double *vel) {
+    int rc = check_replica(s, r);
+    if (rc) return rc;
+    if (s->sticky) return s->sticky;
+    if (!s->loaded[r]) return MD_ESTATE;
+    const int n = s->n[r], o = s->off[r];
+    const size_t R4 = s->r4;
+    std::vector<double> x(n), y(n), z(n);
+    std::vector<int4> img(n);
+    std::vector<int> ids(n);
+    std::vector<unsigned char> vv((size_t)n * R4);
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(s, MD_ECUDA);
+    const Buffers &b = s->b;
+    bool ok = cudaMemcpy(x.data(), b.xd + o, n * 8, cudaMemcpyDeviceToHost) == cudaSuccess;
+    ok = ok && cudaMemcpy(y.data(), b.yd + o, n * 8, cudaMemcpyDeviceToHost) == cudaSuccess;
+    ok = ok && cudaMemcpy(z.data(), b.zd + o, n * 8, cudaMemcpyDeviceToHost) == cudaSuccess;
+    ok = ok && cudaMemcpy(img.data(), b.img + o, n * sizeof(int4), cudaMemcpyDeviceToHost) == cudaSuccess;
+    ok = ok && cudaMemcpy(ids.data(), b.id + o, n * sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess;
+    ok = ok && cudaMemcpy(vv.data(), (char *)b.vel + o * R4, n * R4, cudaMemcpyDeviceToHost) == cudaSuccess;
+    if (!ok) return fail(s, MD_ECUDA);
+    for (int k = 0; k < n; ++k) {
+        const int u = ids[k];
+        if (u < 0 || u >= n) return fail(s, MD_ECUDA);
+        if (pos) { pos[3 * u] = x[k]; pos[3 * u + 1] = y[k]; pos[3 * u + 2] = z[k]; }
+        if (image) { image[3 * u] = img[k].x; image[3 * u + 1] = img[k].y; image[3 * u + 2] = img[k].z; }
+        if (vel) unpack_v4(s, vv, k, vel + 3 * u);
+    }
+    return MD_OK;
+}
+
+int md_get_energies(md_sim *s, int r, md_energies *out) {
+    int rc = check_replica(s, r);
+    if (rc) return rc;
+    if (!out) return MD_EINVAL;
+    if (s->sticky) return s->sticky;
+    Thermo th;
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess ||
+        cudaMemcpy(&th, s->b.th + r, sizeof(th), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(s, MD_ECUDA);
+    const double n = s->n[r], L = s->L[r], g = 3.0 * n - 3.0;
+    std::memset(out, 0, sizeof(*out));
+    out->step = th.step - 1;
+    out->n = s->n[r];
+    out->V = L * L * L;
+    out->U = th.U;
+    out->W = th.W;
+    out->K_minus = th.K_minus;
+    out->K_plus = th.K_plus;
+    out->K = 0.5 * (th.K_minus + th.K_plus);
+    out->T_kin = 2.0 * out->K / g;
+    out->P = (n * out->T_kin + th.W) / out->V;
+    out->xi = th.xi;
+    out->xi_int = th.xi_int;
+    out->H = out->U + out->K;
+    if (s->integrator == MD_NVT_NOSE_HOOVER)
+        out->H += g * s->T0 * (0.5 * s->tau * s->tau * th.xi * th.xi + th.xi_int);
+    out->sum_p[0] = th.px;
+    out->sum_p[1] = th.py;
+    out->sum_p[2] = th.pz;
+    return MD_OK;
+}
+
+int md_get_forces(md_sim *s, int r, double *f, double *u, double *w) {
+    int rc = check_replica(s, r);
+    if (rc) return rc;
+    if (s->sticky) return s->sticky;
+    for (char c : s->loaded)
+        if (!c) return MD_ESTATE;
+    if ((rc = ensure_list(s))) return rc;
+    const int p = (int)(s->h_step & 1);
+    if (do_step(s, p, s->stream, 1) != cudaSuccess) return fail(s, MD_ECUDA);
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(s, MD_ECUDA);
+    const int n = s->n[r], o = s->off[r];
+    const size_t R4 = s->r4;
+    std::vector<unsigned char> fv((size_t)n * R4), wv((size_t)n * (R4 / 4));
+    std::vector<int> ids(n);
+    bool ok = cudaMemcpy(fv.data(), (char *)s->b.f_out + o * R4, n * R4, cudaMemcpyDeviceToHost) == cudaSuccess;
+    ok = ok && cudaMemcpy(wv.data(), (char *)s->b.w_out + o * (R4 / 4), n * (R4 / 4), cudaMemcpyDeviceToHost) == cudaSuccess;
+    ok = ok && cudaMemcpy(ids.data(), s->b.id + o, n * sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess;
+    if (!ok) return fail(s, MD_ECUDA);
+    for (int k = 0; k < n; ++k) {
+        const int q = ids[k];
+        double v4[4];
+        if (s->precision == MD_FP64) {
+            std::memcpy(v4, fv.data() + k * 32, 32);
+        } else {
+            float t[4];
+            std::memcpy(t, fv.data() + k * 16, 16);
+            for (int c = 0; c < 4; ++c) v4[c] = t[c];
+        }
+        if (f) { f[3 * q] = v4[0]; f[3 * q + 1] = v4[1]; f[3 * q + 2] = v4[2]; }
+        if (u) u[q] = v4[3];
+        if (w) {
+            if (s->precision == MD_FP64) {
+                double t;
+                std::memcpy(&t, wv.data() + k * 8, 8);
+                w[q] = t;
+            } else {
+                float t;
+                std::memcpy(&t, wv.data() + k * 4, 4);
+                w[q] = t;
+            }
+        }
+    }
+    return MD_OK;
+}
+
+int md_get_neighbors(md_sim *s, int r, int maxp, int *counts, int *nbrs) {
+    int rc = check_replica(s, r);
+    if (rc) return rc;
+    if (!counts || maxp < 0 || (maxp > 0 && !nbrs)) return MD_EINVAL;
+    if (s->sticky) return s->sticky;
+    const int n = s->n[r], o = s->off[r];
+    std::vector<int> cnt(n), ids(n), lst((size_t)n * s->nmax);
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(s, MD_ECUDA);
+    bool ok = cudaMemcpy(cnt.data(), s->b.nnb + o, n * sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess;
+    ok = ok && cudaMemcpy(ids.data(), s->b.id + o, n * sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess;
+    ok = ok && cudaMemcpy2D(lst.data(), n * sizeof(int), s->b.nbl + o, (size_t)s->ntot * sizeof(int),
+                            n * sizeof(int), s->nmax, cudaMemcpyDeviceToHost) == cudaSuccess;
+    if (!ok) return fail(s, MD_ECUDA);
+    for (int k = 0; k < n; ++k) {
+        const int q = ids[k];
+        counts[q] = cnt[k];
+        for (int m = 0; m < maxp; ++m) {
+            int v = -1;
+            if (m < cnt[k] && m < s->nmax) {
+                const int j = lst[(size_t)m * n + k] - o;
+                v = (j >= 0 && j < n) ? ids[j] : -2;
+            }
+            nbrs[(size_t)q * maxp + m] = v;
+        }
+    }
+    return MD_OK;
+}
+
+int md_set_tuning(md_sim *s, int tp, int block, int reach) {
+    if (!s) return MD_EINVAL;
+    if (s->sticky) return s->sticky;
+    const int ntp = tp ? tp : s->tp, nb = block ? block : s->block, nr = reach ? reach : s->reach;
+    if (!is_pow2_tp(ntp) || nb < 32 || nb > 1024 || (nb % 32) != 0 || nb < ntp || nr < 1 || nr > 3)
+        return MD_EINVAL;
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(s, MD_ECUDA);
+    const bool cells_change = nr != s->reach;
+    s->tp = ntp;
+    s->block = nb;
+    s->reach = nr;
+    destroy_graphs(s);
+    int rc = configure_layout(s, cells_change);
+    if (rc) return rc == MD_ENOMEM ? MD_ENOMEM : fail(s, MD_ECUDA);
+    if (cells_change) return request_rebuild_all(s);
+    return MD_OK;
+}
+
+int md_get_tuning(md_sim *s, int *tp, int *block, int *reach) {
+    if (!s) return MD_EINVAL;
+    if (tp) *tp = s->tp;
+    if (block) *block = s->block;
+    if (reach) *reach = s->reach;
+    return MD_OK;
+}
+
+int md_set_graph_block(md_sim *s, int steps) {
+    if (!s) return MD_EINVAL;
+    if (steps < 0 || (steps > 0 && (steps < 2 || (steps & 1)))) return MD_EINVAL;
+    if (s->sticky) return s->sticky;
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(s, MD_ECUDA);
+    destroy_graphs(s);
+    s->graph_block = steps;
+    return MD_OK;
+}
+
+int md_get_stats(md_sim *s, md_stats *out) {
+    if (!s || !out) return MD_EINVAL;
+    std::memset(out, 0, sizeof(*out));
+    if (s->sticky) return s->sticky;
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(s, MD_ECUDA);
+    std::vector<Thermo> th(s->R);
+    std::vector<int> nn(s->ntot);
+    if (cudaMemcpy(th.data(), s->b.th, sizeof(Thermo) * s->R, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(nn.data(), s->b.nnb, sizeof(int) * s->ntot, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        read_ctrl(s))
+        return fail(s, MD_ECUDA);
+    long long reb = 0, ent = 0;
+    int mx = 0;
+    for (auto &t : th) reb += t.rebuilds;
+    for (int v : nn) { ent += v; mx = std::max(mx, v); }
+    out->steps = s->h_step;
+    out->rebuild_passes = s->h_ctrl->rebuild_passes;
+    out->replica_rebuilds = reb;
+    out->overflows = s->overflows;
+    out->n_max = s->nmax;
+    out->max_neighbors = mx;
+    out->tp = s->tp;
+    out->block = s->block;
+    out->reach = s->reach;
+    out->graph_block = s->graph_block;
+    out->n_total = s->ntot;
+    out->neighbor_entries = ent;
+    return MD_OK;
+}
+
+int md_profile(md_sim *s, int n_steps, md_timing *out) {
+    if (!s || !out || n_steps < 1) return MD_EINVAL;
+    if (s->sticky) return s->sticky;
+    for (char c : s->loaded)
+        if (!c) return MD_ESTATE;
+    std::memset(out, 0, sizeof(*out));
+    double t_step = 0.0, t_reb = 0.0;
+    int n_reb = 0;
+    long long entries = 0;
+    for (int k = 0; k < n_steps; ++k) {
+        int rc = read_ctrl(s);
+        if (rc) return rc;
+        const bool will = s->h_ctrl->need_any && !s->h_ctrl->halt;
+        const int p = (int)(s->h_step & 1);
+        cudaError_t e;
+        if (s->precision == MD_FP64)
+            e = launch_rebuild_timed<double>(rebuild_args<double>(s, p, nullptr), s->stream, s->ev[0], s->ev[1]);
+        else
+            e = launch_rebuild_timed<float>(rebuild_args<float>(s, p, nullptr), s->stream, s->ev[0], s->ev[1]);
+        if (e != cudaSuccess) return fail(s, MD_ECUDA);
+        if (do_step(s, p, s->stream, 0) != cudaSuccess || cudaEventRecord(s->ev[2], s->stream) != cudaSuccess)
+            return fail(s, MD_ECUDA);
+        if ((rc = read_ctrl(s))) return rc;
+        if (s->h_ctrl->unstable) return fail(s, MD_EUNSTABLE);
+        if (s->h_ctrl->overflow) {
+            if ((rc = recover_overflow(s))) return rc;
+            --k;
+            continue;
+        }
+        float a = 0.f, c = 0.f;
+        cudaEventElapsedTime(&a, s->ev[0], s->ev[1]);
+        cudaEventElapsedTime(&c, s->ev[1], s->ev[2]);
+        t_step += c;
+        if (will) { t_reb += a; ++n_reb; }
+        s->h_step += 1;
+    }
+    md_stats st;
+    if (md_get_stats(s, &st) == MD_OK) entries = st.neighbor_entries;
+    out->steps = n_steps;
+    out->step_kernel_ms = t_step / n_steps;
+    out->rebuild_ms = n_reb ? t_reb / n_reb : 0.0;
+    out->rebuild_fraction = (double)n_reb / n_steps;
+    out->neighbor_entries = entries;
+    return MD_OK;
+}
+
+int md_set_log(md_sim *s, int capacity) {
+    if (!s || capacity < 0) return MD_EINVAL;
+    if (s->sticky) return s->sticky;
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(s, MD_ECUDA);
+    dfree(s->b.log);
+    s->log_cap = 0;
+    destroy_graphs(s);
+    if (capacity == 0) return MD_OK;
+    const size_t cnt = (size_t)capacity * s->R * MD_LOG_COLS;
+    if (dalloc(s, &s->b.log, cnt)) return MD_ENOMEM;
+    if (cudaMemset(s->b.log, 0, cnt * sizeof(double)) != cudaSuccess) return fail(s, MD_ECUDA);
+    s->log_cap = capacity;
+    return MD_OK;
+}
+
+int md_get_log(md_sim *s, int r, int max_rows, double *out, int *rows) {
+    int rc = check_replica(s, r);
+    if (rc) return rc;
+    if (!rows || max_rows < 0 || (max_rows > 0 && !out)) return MD_EINVAL;
+    *rows = 0;
+    if (s->sticky) return s->sticky;
+    if (s->log_cap == 0) return MD_OK;
+    Thermo th;
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess ||
+        cudaMemcpy(&th, s->b.th + r, sizeof(th), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(s, MD_ECUDA);
+    const long long done = th.step;
+    const long long k = std::min<long long>(std::min<long long>(done, s->log_cap), max_rows);
+    std::vector<double> all((size_t)s->log_cap * s->R * MD_LOG_COLS);
+    if (cudaMemcpy(all.data(), s->b.log, all.size() * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(s, MD_ECUDA);
+    for (long long q = 0; q < k; ++q) {
+        const long long step = done - k + q;
+        const double *row = all.data() + ((size_t)(step % s->log_cap) * s->R + r) * MD_LOG_COLS;
+        std::memcpy(out + q * MD_LOG_COLS, row, sizeof(double) * MD_LOG_COLS);
+    }
+    *rows = (int)k;
+    return MD_OK;
+}
+
+// ---------------------------------------------------------------- checkpoints
+// Layout: header, then per replica: Thermo, need flag, and per particle (user order):
+// x y z (double), image (3 int), type (int), velocity (3 Real), build position (3 Real).
+namespace {
+struct CkHeader {
+    char magic[8];
+    int version, R, ntot, precision, nt, pad;
+    long long step;
+};
+size_t ck_bytes(const md_sim *s) {
+    size_t b = sizeof(CkHeader) + (size_t)s->R * (sizeof(Thermo) + sizeof(int));
+    const size_t rsz = s->precision == MD_FP64 ? 8 : 4;
+    b += (size_t)s->ntot * (3 * 8 + 4 * 4 + 6 * rsz);
+    return b;
+}
+}  // namespace
+
+int md_checkpoint_size(md_sim *s, size_t *bytes) {
+    if (!s || !bytes) return MD_EINVAL;
+    *bytes = ck_bytes(s);
+    return MD_OK;
+}
+
+int md_save_checkpoint(md_sim *s, void *buf, size_t bytes) {
+    if (!s || !buf || bytes < ck_bytes(s)) return MD_EINVAL;
+    if (s->sticky) return s->sticky;
+    for (char c : s->loaded)
+        if (!c) return MD_ESTATE;
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(s, MD_ECUDA);
+    const size_t N = s->ntot, R4 = s->r4, rsz = R4 / 4;
+    std::vector<double> x(N), y(N), z(N);
+    std::vector<int4> img(N);
+    std::vector<int> ids(N), need(s->R);
+    std::vector<unsigned char> vel(N * R4), pb(N * R4), cur(N * R4);
+    std::vector<Thermo> th(s->R);
+    const Buffers &b = s->b;
+    bool ok = cudaMemcpy(x.data(), b.xd, N * 8, cudaMemcpyDeviceToHost) == cudaSuccess;
+    ok = ok && cudaMemcpy(cur.data(), b.pos[s->h_step & 1], N * R4, cudaMemcpyDeviceToHost) ==
+                   cudaSuccess;
+    ok = ok && cudaMemcpy(y.data(), b.yd, N * 8, cudaMemcpyDeviceToHost) == cudaSuccess;
+    ok = ok && cudaMemcpy(z.data(), b.zd, N * 8, cudaMemcpyDeviceToHost) == cudaSuccess;
+    ok = ok && cudaMemcpy(img.data(), b.img, N * sizeof(int4), cudaMemcpyDeviceToHost) == cudaSuccess;
+    ok = ok && cudaMemcpy(ids.data(), b.id, N * sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess;
+    ok = ok && cudaMemcpy(vel.data(), b.vel, N * R4, cudaMemcpyDeviceToHost) == cudaSuccess;
+    ok = ok && cudaMemcpy(pb.data(), b.pos_build, N * R4, cudaMemcpyDeviceToHost) == cudaSuccess;
+    ok = ok && cudaMemcpy(th.data(), b.th, sizeof(Thermo) * s->R, cudaMemcpyDeviceToHost) == cudaSuccess;
+    ok = ok && cudaMemcpy(need.data(), b.need, sizeof(int) * s->R, cudaMemcpyDeviceToHost) == cudaSuccess;
+    if (!ok) return fail(s, MD_ECUDA);
+    unsigned char *p = (unsigned char *)buf;
+    CkHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, "MDGB300", 8);
+    h.version = 1; h.R = s->R; h.ntot = s->ntot; h.precision = s->precision; h.nt = s->nt;
+    h.step = s->h_step;
+    std::memcpy(p, &h, sizeof(h));
+    p += sizeof(h);
+    for (int r = 0; r < s->R; ++r) {
+        std::memcpy(p, &th[r], sizeof(Thermo)); p += sizeof(Thermo);
+        std::memcpy(p, &need[r], sizeof(int)); p += sizeof(int);
+    }
+    // per particle records in user order
+    const size_t rec = 3 * 8 + 4 * 4 + 6 * rsz;
+    for (int r = 0; r < s->R; ++r) {
+        const int o = s->off[r], n = s->n[r];
+        for (int k = 0; k < n; ++k) {
+            const int q = ids[o + k];
+            if (q < 0 || q >= n) return fail(s, MD_ECUDA);
+            unsigned char *d = p + (size_t)(o + q) * rec;
+            const size_t sl = o + k;
+            std::memcpy(d, &x[sl], 8); std::memcpy(d + 8, &y[sl], 8); std::memcpy(d + 16, &z[sl], 8);
+            int im[4] = {img[sl].x, img[sl].y, img[sl].z, 0};
+            if (s->precision == MD_FP64) {
+                long long t;
+                std::memcpy(&t, cur.data() + sl * 32 + 24, 8);
+                im[3] = (int)t;
+            } else {
+                std::memcpy(&im[3], cur.data() + sl * 16 + 12, 4);
+            }
+            std::memcpy(d + 24, im, 16);
+            std::memcpy(d + 40, vel.data() + sl * R4, 3 * rsz);
+            std::memcpy(d + 40 + 3 * rsz, pb.data() + sl * R4, 3 * rsz);
+        }
+    }
+    return MD_OK;
+}
+
+int md_load_checkpoint(md_sim *s, const void *buf, size_t bytes) {
+    if (!s || !buf || bytes < ck_bytes(s)) return MD_EINVAL;
+    if (s->sticky) return s->sticky;
+    const unsigned char *p = (const unsigned char *)buf;
+    CkHeader h;
+    std::memcpy(&h, p, sizeof(h));
+    p += sizeof(h);
+    if (std::memcmp(h.magic, "MDGB300", 8) != 0 || h.version != 1 || h.R != s->R ||
+        h.ntot != s->ntot || h.precision != s->precision || h.nt != s->nt)
+        return MD_EINVAL;
+    const size_t N = s->ntot, R4 = s->r4, rsz = R4 / 4;
+    std::vector<Thermo> th(s->R);
+    std::vector<int> need(s->R);
+    for (int r = 0; r < s->R; ++r) {
+        std::memcpy(&th[r], p, sizeof(Thermo)); p += sizeof(Thermo);
+        std::memcpy(&need[r], p, sizeof(int)); p += sizeof(int);
+    }
+    std::vector<double> x(N), y(N), z(N);
+    std::vector<int4> img(N);
+    std::vector<int> ids(N);
+    std::vector<unsigned char> mirror(N * R4), vel(N * R4), pb(N * R4);
+    std::vector<int> types(N);
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(s, MD_ECUDA);
+    const size_t rec = 3 * 8 + 4 * 4 + 6 * rsz;
+    for (int r = 0; r < s->R; ++r) {
+        const int o = s->off[r], n = s->n[r];
+        for (int q = 0; q < n; ++q) {
+            const unsigned char *d = p + (size_t)(o + q) * rec;
+            const size_t sl = o + q;   // load in user order; the restore rebuild sorts
+            std::memcpy(&x[sl], d, 8); std::memcpy(&y[sl], d + 8, 8); std::memcpy(&z[sl], d + 16, 8);
+            int im[4];
+            std::memcpy(im, d + 24, 16);
+            img[sl] = make_int4(im[0], im[1], im[2], 0);
+            types[sl] = im[3];
+            if (im[3] < 0 || im[3] >= s->nt) return MD_EINVAL;
+            ids[sl] = q;
+            pack_pos(s, mirror, sl, x[sl], y[sl], z[sl], types[sl]);
+            std::memset(vel.data() + sl * R4, 0, R4);
+            std::memcpy(vel.data() + sl * R4, d + 40, 3 * rsz);
+            double bx[3];
+            if (rsz == 8) {
+                std::memcpy(bx, d + 40 + 3 * rsz, 24);
+            } else {
+                float t3[3];
+                std::memcpy(t3, d + 40 + 3 * rsz, 12);
+                bx[0] = t3[0]; bx[1] = t3[1]; bx[2] = t3[2];
+            }
+            pack_pos(s, pb, sl, bx[0], bx[1], bx[2], types[sl]);
+        }
+    }
+    s->h_step = h.step;
+    const int cur = (int)(s->h_step & 1);
+    Buffers &b = s->b;
+    bool ok = cudaMemcpy(b.pos[cur], mirror.data(), N * R4, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemcpy(b.pos_build, pb.data(), N * R4, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemcpy(b.xd, x.data(), N * 8, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemcpy(b.yd, y.data(), N * 8, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemcpy(b.zd, z.data(), N * 8, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemcpy(b.vel, vel.data(), N * R4, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemcpy(b.img, img.data(), N * sizeof(int4), cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemcpy(b.id, ids.data(), N * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemcpy(b.th, th.data(), sizeof(Thermo) * s->R, cudaMemcpyHostToDevice) == cudaSuccess;
+    Ctrl c;
+    std::memset(&c, 0, sizeof(c));
+    c.step = h.step;
+    c.need_any = 1;
+    ok = ok && cudaMemcpy(b.ctrl, &c, sizeof(c), cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemset(b.moved, 0, sizeof(int) * s->R) == cudaSuccess;
+    ok = ok && cudaMemset(b.ticket, 0, sizeof(unsigned) * s->R) == cudaSuccess;
+    if (!ok) return fail(s, MD_ECUDA);
+    int rc = request_rebuild_all(s);
+    if (rc) return rc;
+    // restore rebuild: cells, order and list from the saved build positions
+    for (int tries = 0; tries < 16; ++tries) {
+        cudaError_t e = do_rebuild(s, cur, s->stream, s->b.pos_build);
+        if (e != cudaSuccess) return fail(s, MD_ECUDA);
+        if ((rc = read_ctrl(s))) return rc;
+        if (!s->h_ctrl->overflow) break;
+        if ((rc = recover_overflow(s))) return rc;
+    }
+    // pending rebuild flags as saved
+    int any = 0;
+    for (int v : need) any |= v;
+    ok = cudaMemcpy(b.need, need.data(), sizeof(int) * s->R, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemcpy(&b.ctrl->need_any, &any, sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) return fail(s, MD_ECUDA);
+    destroy_graphs(s);
+    for (auto &l : s->loaded) l = 1;
+    return MD_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- autotuner (Appendix)
+// Short timed runs from one saved state (restored before every trial, so every trial starts from
+// the same configuration), a line search over the cell stencil reach, then the double loop of
+// the Appendix over block size and threads per particle with its break rules:
+//   - the tp loop stops when the time exceeds the best so far three times in a row, or exceeds it
+//     by 5%, or the block cannot hold the group;
+//   - the block loop stops when its best exceeds the overall best by 10% or more.
+// The result is cached in a text file keyed by the "user parameters" (particle counts per type
+// and replica, densities, potential, integrator, dt, temperature) and the GPU name.
+namespace {
+
+std::string tune_key(md_sim *s) {
+    cudaDeviceProp prop;
+    std::memset(&prop, 0, sizeof(prop));
+    cudaGetDeviceProperties(&prop, s->device);
+    // FNV-1a over the replica sizes and boxes keeps the key short for large ensembles
+    unsigned long long h = 1469598103934665603ULL;
+    auto mix = [&h](const void *p, size_t n) {
+        const unsigned char *c = (const unsigned char *)p;
+        for (size_t k = 0; k < n; ++k) { h ^= c[k]; h *= 1099511628211ULL; }
+    };
+    for (int r = 0; r < s->R; ++r) {
+        mix(&s->n[r], sizeof(int));
+        const float Lr = (float)s->L[r];   // density within float tolerance
+        mix(&Lr, sizeof(float));
+    }
+    for (auto &p : s->params) {
+        const float q[3] = {(float)p.eps, (float)p.sigma, (float)p.rc};
+        mix(q, sizeof(q));
+    }
+    char buf[512];
+    std::snprintf(buf, sizeof(buf), "gpu=%s|R=%d|N=%d|nt=%d|prec=%d|skin=%.4g|integ=%d|dt=%.6g|T=%.4g|h=%016llx",
+                  prop.name, s->R, s->ntot, s->nt, s->precision, s->skin, s->integrator, s->dt,
+                  s->integrator == MD_NVT_NOSE_HOOVER ? s->T0 : 0.0, h);
+    std::string k(buf);
+    for (char &c : k)
+        if (c == ' ') c = '_';
+    return k;
+}
+
+bool cache_lookup(const char *path, const std::string &key, int *tp, int *block, int *reach) {
+    if (!path) return false;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return false;
+    char line[1024];
+    bool found = false;
+    while (std::fgets(line, sizeof(line), f)) {
+        char k[900];
+        int a, b, c;
+        if (std::sscanf(line, "%899s %d %d %d", k, &a, &b, &c) == 4 && key == k) {
+            *tp = a; *block = b; *reach = c;
+            found = true;   // the last entry for a key wins
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+void cache_store(const char *path, const std::string &key, int tp, int block, int reach, double ms) {
+    if (!path) return;
+    FILE *f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%s %d %d %d %.6f\n", key.c_str(), tp, block, reach, ms);
+    std::fclose(f);
+}
+
+}  // namespace
+
+extern "C" int md_autotune(md_sim *s, const char *cache_path, int steps) {
+    if (!s || steps < 2) return MD_EINVAL;
+    if (s->sticky) return s->sticky;
+    for (char c : s->loaded)
+        if (!c) return MD_ESTATE;
+    const std::string key = tune_key(s);
+    int tp = 0, block = 0, reach = 0;
+    if (cache_lookup(cache_path, key, &tp, &block, &reach) && is_pow2_tp(tp) && block >= tp &&
+        block <= 1024 && block % 32 == 0 && reach >= 1 && reach <= 3)
+        return md_set_tuning(s, tp, block, reach);
+    size_t bytes = 0;
+    md_checkpoint_size(s, &bytes);
+    std::vector<unsigned char> ck(bytes);
+    int rc = md_save_checkpoint(s, ck.data(), bytes);
+    if (rc) return rc;
+    const int gb_saved = s->graph_block;
+    const int gb = (steps >= 4) ? (steps / 2) * 2 : 2;
+    int trial_block = std::min(gb, 50);
+    if (trial_block & 1) --trial_block;
+    // time one configuration: restore, warm up (graph capture + first rebuild), restore, time
+    auto trial = [&](int t, int b, int re, double *ms) -> int {
+        int e = md_set_tuning(s, t, b, re);
+        if (e) return e;
+        if ((e = md_set_graph_block(s, trial_block))) return e;
+        if ((e = md_load_checkpoint(s, ck.data(), bytes))) return e;
+        if ((e = md_step(s, trial_block))) return e;
+        if ((e = md_load_checkpoint(s, ck.data(), bytes))) return e;
+        if (cudaEventRecord(s->ev[0], s->stream) != cudaSuccess) return fail(s, MD_ECUDA);
+        if ((e = md_step(s, steps))) return e;
+        if (cudaEventRecord(s->ev[1], s->stream) != cudaSuccess ||
+            cudaEventSynchronize(s->ev[1]) != cudaSuccess)
+            return fail(s, MD_ECUDA);
+        float f = 0.f;
+        cudaEventElapsedTime(&f, s->ev[0], s->ev[1]);
+        *ms = f / steps;
+        return MD_OK;
+    };
+    int nmax_part = 0;
+    for (int v : s->n) nmax_part = std::max(nmax_part, v);
+    // Appendix defaults: t_p = 4 (p_b = 32) up to 10^4 particles, else t_p = 1 (p_b = 64)
+    int best_tp = nmax_part <= 10000 ? 4 : 1, best_block = nmax_part <= 10000 ? 128 : 64;
+    int best_reach = 2;
+    double best = 1e30, t = 0.0;
+    // phase I: stencil reach at default kernel shape
+    for (int re : {2, 1, 3}) {
+        if ((rc = trial(best_tp, best_block, re, &t))) return rc;
+        if (t < best) { best = t; best_reach = re; }
+    }
+    // phase II: block size x threads per particle
+    const int blocks[] = {64, 128, 256, 512};
+    for (int b : blocks) {
+        double best_b = 1e30;
+        int worse = 0;
+        for (int tpv = 1; tpv <= 32; tpv *= 2) {
+            if (tpv > b) break;
+            if (nmax_part > 100000 && tpv > 1) break;   // Appendix: only t_p = 1 for N > 1e5
+            if ((rc = trial(tpv, b, best_reach, &t))) return rc;
+            if (t < best_b) best_b = t;
+            if (t < best) { best = t; best_tp = tpv; best_block = b; worse = 0; continue; }
+            if (t > 1.05 * best || ++worse >= 3) break;
+        }
+        if (best_b >= 1.10 * best) break;
+    }
+    if ((rc = md_set_tuning(s, best_tp, best_block, best_reach))) return rc;
+    if ((rc = md_set_graph_block(s, gb_saved))) return rc;
+    if ((rc = md_load_checkpoint(s, ck.data(), bytes))) return rc;
+    cache_store(cache_path, key, best_tp, best_block, best_reach, best);
+    return MD_OK;
+}

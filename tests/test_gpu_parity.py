@@ -1,0 +1,334 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle on the same seeded
+inputs.
+
+Tolerances (mixed precision, as the precision contract states them):
+  forces   : relative RMS  ||F_gpu - F_ref||_2 / ||F_ref||_2 <= 1e-5
+  U        : relative      <= 1e-6
+  W        : |W_gpu - W_ref| <= 1e-6 * sum_i |w_i|  (W itself may be near zero)
+  FP64 mode: the same quantities to 1e-12.
+The oracle is fed the positions the device holds (FP32 mirror of the FP64 master positions for
+the mixed path), so the comparison measures arithmetic, not input rounding; the error against the
+unrounded FP64 positions is checked as a second, looser number.
+Neighbour pair sets (integer) must be equal bit for bit to the oracle's FP32 brute force.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import f32, ka, lj, make_sim, rel_rms
+
+pytestmark = pytest.mark.gpu
+
+KA = synth.ka_model()
+LJ = synth.lj_model()
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    import __graft_entry__
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    __graft_entry__.build()
+
+
+def _check_forces(sim, st, model, r=0, tol=1e-5, utol=1e-6, pos_dev=None):
+    f, u, w = sim.forces(r)
+    pos_dev = f32(st.pos) if pos_dev is None else pos_dev
+    fr, ur, wr, U, W = oracle.forces(pos_dev, st.types, st.L, model)
+    assert rel_rms(f, fr) <= tol, rel_rms(f, fr)
+    assert abs(u.sum() - U) <= utol * abs(U), (u.sum(), U)
+    assert abs(w.sum() - W) <= utol * np.abs(wr).sum(), (w.sum(), W)
+    return f, fr
+
+
+# ------------------------------------------------------------------------------------------ forces
+
+def test_forces_lj1000_mixed():
+    st = synth.workload("lj1000").states[0]
+    with make_sim(LJ, [st]) as sim:
+        f, fr = _check_forces(sim, st, LJ)
+        # against the unrounded FP64 positions (input rounding included): looser
+        fr64 = oracle.forces(st.pos, st.types, st.L, LJ)[0]
+        assert rel_rms(f, fr64) < 1e-4
+
+
+@pytest.mark.parametrize("tp", [1, 2, 4, 8, 16, 32])
+def test_forces_ragged_ka_all_tp(tp):
+    st = ka(777, seed=3)      # 777 = 6 tiles of 128 + a ragged tail at tp = 1
+    with make_sim(KA, [st], tuning=(tp, 128, 2)) as sim:
+        _check_forces(sim, st, KA)
+
+
+@pytest.mark.parametrize("reach,block", [(1, 64), (2, 256), (3, 1024)])
+def test_forces_cell_reach_and_block(reach, block):
+    st = ka(2000, seed=5)
+    with make_sim(KA, [st], tuning=(4, block, reach)) as sim:
+        _check_forces(sim, st, KA)
+
+
+def test_forces_fp64_mode():
+    st = ka(1500, seed=8)
+    with make_sim(KA, [st], precision="fp64") as sim:
+        f, u, w = sim.forces(0)
+        fr, ur, wr, U, W = oracle.forces(st.pos, st.types, st.L, KA)
+        assert rel_rms(f, fr) < 1e-12
+        assert abs(u.sum() - U) < 1e-12 * abs(U)
+        np.testing.assert_allclose(u, ur, rtol=1e-11, atol=1e-13)
+
+
+def test_forces_ka8000():
+    st = synth.workload("ka8000").states[0]
+    with make_sim(KA, [st]) as sim:
+        _check_forces(sim, st, KA)
+
+
+def test_forces_large_sampled():
+    """LJ N = 131072 (fcc 32^3 after a short melt): sampled particles against the oracle."""
+    st = synth.workload("lj131072").states[0]
+    with make_sim(LJ, [st]) as sim:
+        sim.step(20)
+        pos, img, vel = sim.get_state(0)
+        f, u, w = sim.forces(0)
+        idx = np.random.default_rng(0).choice(st.n, 64, replace=False)
+        fr, ur, wr = oracle.forces_subset(f32(pos), st.types, st.L, LJ, idx)
+        assert rel_rms(f[idx], fr) < 1e-5
+        np.testing.assert_allclose(u[idx], ur, rtol=2e-5, atol=2e-6)
+
+
+# ------------------------------------------------------------------------------------ pair sets
+
+@pytest.mark.parametrize("n,reach", [(1000, 2), (1000, 1), (1000, 3), (256, 2), (600, 2)])
+def test_neighbor_sets_bit_exact(n, reach):
+    """Cell-list build == brute force in the same FP32 arithmetic (n = 256 has 4 cells/edge,
+    so the +-2 stencil wraps onto itself and must visit each cell once)."""
+    st = ka(n, seed=11 + n)
+    with make_sim(KA, [st], tuning=(1, 128, reach)) as sim:
+        sim.forces(0)     # builds the list
+        counts, nb = sim.neighbors(0)
+    ref, rc = oracle.neighbors_fp32(f32(st.pos), st.types, st.L, KA, 0.3)
+    np.testing.assert_array_equal(counts, rc)
+    for i in range(n):
+        got = np.sort(nb[i, :counts[i]])
+        np.testing.assert_array_equal(got, ref[i])
+
+
+def test_neighbor_sets_fp64_mode_near_threshold_only():
+    st = ka(1000, seed=13)
+    with make_sim(KA, [st], precision="fp64") as sim:
+        sim.forces(0)
+        counts, nb = sim.neighbors(0)
+    ref, rc = oracle.neighbors_fp64(st.pos, st.types, st.L, KA, 0.3)
+    for i in range(st.n):
+        assert set(nb[i, :counts[i]].tolist()) == set(ref[i].tolist())
+
+
+# ---------------------------------------------------------------------------------- trajectories
+
+def test_first_step_energies_match_oracle():
+    st = ka(1200, seed=17)
+    with make_sim(KA, [st], integrator="nvt", dt=0.0025, T=0.8, tau=0.2) as sim:
+        sim.step(1)
+        e = sim.energies(0)
+    run = oracle.Run(f32(st.pos), f32(st.vel), st.types, st.L, KA, "nvt", 0.0025, T=0.8, tau=0.2)
+    log = run.run(1)
+    assert e["step"] == 0
+    assert e["U"] == pytest.approx(log[0, 0], rel=1e-6)
+    assert e["K_minus"] == pytest.approx(log[0, 2], rel=1e-7)
+    assert e["K_plus"] == pytest.approx(log[0, 3], rel=1e-6)
+    assert e["xi"] == pytest.approx(log[0, 4], rel=1e-9, abs=1e-12)
+
+
+def _envelope(st, model, integ, dt, T, nsteps, every, delta):
+    """RMS divergence of two oracle runs whose positions differ by a relative delta."""
+    a = oracle.Run(st.pos, st.vel, st.types, st.L, model, integ, dt, T=T)
+    rng = np.random.default_rng(99)
+    b = oracle.Run(st.pos * (1 + delta * rng.standard_normal(st.pos.shape)), st.vel, st.types,
+                   st.L, model, integ, dt, T=T)
+    out = []
+    for _ in range(nsteps // every):
+        a.run(every)
+        b.run(every)
+        out.append(np.sqrt(np.mean((a.pos - b.pos) ** 2)))
+    return np.array(out)
+
+
+def _gpu_vs_oracle(st, model, precision, integ, dt, T, nsteps, every):
+    vel = f32(st.vel) if precision == "mixed" else st.vel
+    pos = st.pos
+    ref = oracle.Run(pos, vel, st.types, st.L, model, integ, dt, T=T)
+    out = []
+    with make_sim(model, [st], precision=precision, integrator=integ, dt=dt, T=T,
+                  graph_block=every if every % 2 == 0 else 0) as sim:
+        for _ in range(nsteps // every):
+            sim.step(every)
+            ref.run(every)
+            x, _ = sim.unwrapped(0)
+            out.append(np.sqrt(np.mean((x - ref.pos) ** 2)))
+    return np.array(out)
+
+
+def test_nve_trajectory_divergence_bounded():
+    """Mixed precision, LJ N = 1000 melting fcc, 1000 steps: RMS position divergence from the FP64
+    oracle stays within 10x the oracle's own divergence under a 1e-7 relative perturbation."""
+    st = synth.workload("lj1000").states[0]
+    d = _gpu_vs_oracle(st, LJ, "mixed", "nve", 0.005, 0.72, 1000, 100)
+    env = _envelope(st, LJ, "nve", 0.005, 0.72, 1000, 100, 1e-7)
+    assert np.all(d <= 10 * env + 1e-6), (d, env)
+
+
+def test_fp64_trajectory_tracks_oracle():
+    """FP64 mode, LJ N = 1000, 1000 steps: divergence within 10x the oracle's FP64 envelope
+    (1e-15 relative perturbation) and below 1e-9 for the first 500 steps."""
+    st = synth.workload("lj1000").states[0]
+    d = _gpu_vs_oracle(st, LJ, "fp64", "nve", 0.005, 0.72, 1000, 100)
+    env = _envelope(st, LJ, "nve", 0.005, 0.72, 1000, 100, 1e-15)
+    assert np.all(d <= 10 * env + 1e-12), (d, env)
+    assert np.all(d[:5] < 1e-9), d
+
+
+def test_nvt_ka_thermostat_and_conserved_H():
+    st = ka(1000, T=0.8, seed=21)
+    with make_sim(KA, [st], integrator="nvt", dt=0.0025, T=0.8, tau=0.2, graph_block=100) as sim:
+        sim.set_log(4000)
+        sim.step(4000)
+        log = sim.get_log(0)
+    g = 3 * st.n - 3
+    Tk = (log[:, 3] + log[:, 4]) / g
+    assert np.mean(Tk[1500:]) == pytest.approx(0.8, rel=0.05)
+    H, U = log[:, 7], log[:, 1]
+    assert np.ptp(H[500:]) < 0.1 * np.ptp(U[500:])
+
+
+def test_nve_energy_drift_small():
+    st = synth.workload("lj1000").states[0]
+    with make_sim(LJ, [st], integrator="nve", dt=0.005, graph_block=100) as sim:
+        sim.set_log(10000)
+        sim.step(10000)
+        log = sim.get_log(0)
+    E = log[:, 7] / st.n
+    slope = np.polyfit(np.arange(len(E)) * 0.005, E, 1)[0]
+    print(f"NVE drift LJ N=1000 FP32 pair math: {slope:.3e} per particle per unit time")
+    assert abs(slope) < 1e-4, slope          # per particle per unit time
+    # a full list has no pairwise cancellation of FP32 rounding, so sum p random-walks slowly:
+    # bound it by FP32 rounding of the momentum scale sum_i |p_i| ~ N sqrt(3 T)
+    p = np.abs(log[:, 8:11]).max()
+    print(f"max |sum p| over 1e4 steps: {p:.3e}")
+    assert p < 1e-5 * st.n * np.sqrt(3 * 0.72)
+
+
+# ------------------------------------------------------------------------------- determinism
+
+def _run_bits(st, model, steps, **kw):
+    with make_sim(model, [st], **kw) as sim:
+        sim.step(steps)
+        pos, img, vel = sim.get_state(0)
+        e = sim.energies(0)
+    return pos, img, vel, e
+
+
+def test_graph_and_plain_launches_bit_identical():
+    st = ka(900, seed=23)
+    a = _run_bits(st, KA, 200, integrator="nvt", dt=0.0025, T=0.8, graph_block=50)
+    b = _run_bits(st, KA, 200, integrator="nvt", dt=0.0025, T=0.8, graph_block=0)
+    for x, y in zip(a[:3], b[:3]):
+        np.testing.assert_array_equal(x, y)
+    assert a[3]["U"] == b[3]["U"] and a[3]["xi"] == b[3]["xi"]
+
+
+def test_batched_replicas_equal_single_runs():
+    """Replicas inside a batch follow exactly (bitwise) the trajectory they follow alone."""
+    sts = [ka(n, seed=30 + k) for k, n in enumerate([512, 700, 1024, 900])]
+    with make_sim(KA, sts, integrator="nvt", dt=0.0025, T=0.8, graph_block=20) as sim:
+        sim.step(100)
+        batch = [sim.get_state(r) for r in range(len(sts))]
+        eb = [sim.energies(r) for r in range(len(sts))]
+    for r, st in enumerate(sts):
+        pos, img, vel, e = _run_bits(st, KA, 100, integrator="nvt", dt=0.0025, T=0.8,
+                                     graph_block=20)
+        np.testing.assert_array_equal(batch[r][0], pos)
+        np.testing.assert_array_equal(batch[r][2], vel)
+        assert eb[r]["U"] == e["U"]
+
+
+def test_batched_replicas_match_oracle():
+    sts = [ka(n, seed=40 + k) for k, n in enumerate([512, 1000, 777])]
+    with make_sim(KA, sts) as sim:
+        for r, st in enumerate(sts):
+            _check_forces(sim, st, KA, r=r)
+
+
+def test_checkpoint_resume_bit_identical():
+    st = ka(1000, seed=50)
+    kw = dict(integrator="nvt", dt=0.0025, T=0.8, graph_block=10)
+    with make_sim(KA, [st], **kw) as sim:
+        sim.step(137)
+        blob = sim.save_checkpoint()
+        sim.step(263)
+        ref = sim.get_state(0), sim.energies(0)
+    with make_sim(KA, [ka(1000, seed=51)], **kw) as sim2:
+        sim2.load_checkpoint(blob)
+        sim2.step(263)
+        got = sim2.get_state(0), sim2.energies(0)
+    for x, y in zip(ref[0], got[0]):
+        np.testing.assert_array_equal(x, y)
+    assert ref[1]["U"] == got[1]["U"] and ref[1]["xi"] == got[1]["xi"]
+
+
+# ------------------------------------------------------------------------- rebuild / recovery
+
+def test_rebuild_happens_only_past_half_skin():
+    """Sec. 6: rebuild exactly when some particle moved more than s/2 since the last build."""
+    st = synth.State(L=10.0, pos=np.array([[2.0, 2.0, 2.0], [7.0, 7.0, 7.0]]),
+                     vel=np.zeros((2, 3)), types=np.zeros(2, np.int32))
+    st.vel[0, 0] = 1.0      # moves 0.005 per step; s/2 = 0.15 -> 30 steps
+    with make_sim(LJ, [st], integrator="nve", dt=0.005, graph_block=0) as sim:
+        sim.step(1)
+        base = sim.stats()["replica_rebuilds"]
+        sim.step(28)        # displacement 29 * 0.005 = 0.145 < 0.15 at the check after step 29
+        assert sim.stats()["replica_rebuilds"] == base
+        sim.step(3)         # passes 0.15 -> one rebuild
+        assert sim.stats()["replica_rebuilds"] == base + 1
+
+
+def test_overflow_recovers_to_identical_forces():
+    """Sec. 4: an overfull list doubles its capacity and rebuilds; results are unaffected."""
+    st = ka(1200, rho=1.2, seed=60)
+    dense = st.pos.copy()
+    dense[:, 0] = dense[:, 0] * 0.55          # crush into about half the box: ~2x local density
+    st2 = synth.State(L=st.L, pos=dense, vel=st.vel, types=st.types)
+    with make_sim(KA, [st2]) as sim:
+        n0 = sim.stats()["n_max"]
+        f, u, w = sim.forces(0)
+        s = sim.stats()
+        assert s["overflows"] >= 1 and s["n_max"] > n0
+        fr, ur, wr, U, W = oracle.forces(f32(dense), st.types, st.L, KA)
+        assert rel_rms(f, fr) <= 1e-5
+
+
+def test_runaway_displacement_is_reported():
+    from paper_1506_05094_gb300 import MDError
+
+    st = synth.State(L=10.0, pos=np.array([[2.0, 2.0, 2.0], [2.3, 2.0, 2.0], [7.0, 7.0, 7.0]]),
+                     vel=np.zeros((3, 3)), types=np.zeros(3, np.int32))
+    with make_sim(LJ, [st], integrator="nve", dt=0.005) as sim:
+        with pytest.raises(MDError) as ex:
+            sim.step(1)
+        assert ex.value.code == 4
+
+
+def test_autotune_runs_and_caches(tmp_path):
+    st = ka(3000, seed=70)
+    cache = tmp_path / "tune.txt"
+    with make_sim(KA, [st], integrator="nvt", dt=0.0025, T=0.8) as sim:
+        before = sim.get_state(0)
+        tp, block, reach = sim.autotune(str(cache), steps_per_trial=20)
+        after = sim.get_state(0)
+        for x, y in zip(before, after):
+            np.testing.assert_array_equal(x, y)      # the search leaves the state unchanged
+        _check_forces(sim, st, KA)
+    assert cache.exists() and cache.read_text().strip()
+    with make_sim(KA, [st], integrator="nvt", dt=0.0025, T=0.8) as sim2:
+        assert sim2.autotune(str(cache), steps_per_trial=20) == (tp, block, reach)
