@@ -311,7 +311,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip single-system/e2e/cpu legs")
     ap.add_argument("--replicas", type=int, default=None, help="trim the ensemble (profiling)")
-    ap.add_argument("--tuning", default=None, help="tp,block,reach: skip the autotuner")
+    ap.add_argument("--tuning", default=None, help="tp,block,reach[,lanes]: skip the autotuner")
+    ap.add_argument("--path", default=None, choices=["grid", "replica"],
+                    help="force a kernel path (default: the autotuner's choice)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -341,9 +343,14 @@ def main():
     sim = make_sim(wl, stream.cuda_stream)
     if args.tuning:
         tuning = tuple(int(x) for x in args.tuning.split(","))
+        tuning = tuning + (0,) * (4 - len(tuning))
         sim.set_tuning(*tuning)
+        tuning = sim.get_tuning()
     else:
         tuning = sim.autotune(os.path.join(ROOT, "paper_1506_05094_gb300", "tune_cache.txt"), 50)
+    if args.path:
+        sim.set_path(args.path)
+    path = "replica" if sim.stats()["path"] == 2 else "grid"
     gb = pick_block(args.steps)
     sim.set_graph_block(gb)
     sim.step(gb)                     # capture the graph (setup, untimed)
@@ -371,7 +378,10 @@ def main():
     # an odd K ends with one plain step (its 6 rebuild kernels launch and exit if not needed)
     n_graphs = args.steps // gb
     rem = args.steps - n_graphs * gb
-    gpu_launches = args.steps + n_graphs + 6 * passes + 6 * rem
+    if path == "replica":   # one replica-resident launch per step, rebuilds inside it
+        gpu_launches = args.steps
+    else:                   # + arm kernel per graph, 7-kernel rebuild pass per IF body executed
+        gpu_launches = args.steps + n_graphs + 7 * passes + 7 * rem
 
     # dominant kernel: fused step kernel, plain launches with CUDA events on the sim's stream
     prof = sim.profile(50)
@@ -446,7 +456,8 @@ def main():
                 "config": {"workload": "KA ensemble: 512 replicas, N_r~U{512..4096} seed 1004, "
                                        "rho=1.2, NVT T=0.8 dt=0.0025 skin=0.3",
                            "particles_per_gpu": n_total, "replicas": len(wl.states),
-                           "graph_block": gb, "tuning_tp_block_reach": list(tuning),
+                           "graph_block": gb, "tuning_tp_block_reach_lanes": list(tuning),
+                           "kernel_path": path,
                            "precision": "FP32 pair math, FP64 positions and reductions",
                            "l2": "no flush: neighbour list %.2f GB > 129 MB L2"
                                  % (4.0 * st1["neighbor_entries"] / 1e9),

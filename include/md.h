@@ -89,6 +89,8 @@ typedef struct {
     int n_max;                  /* current neighbour-list capacity per particle */
     int max_neighbors;          /* largest neighbour count at the most recent build */
     int tp, block, reach;       /* threads per particle, threads per block, cell stencil reach */
+    int build_lanes;            /* lanes per particle in the list build */
+    int path;                   /* 1 grid kernels, 2 replica-resident kernel */
     int graph_block;            /* steps per captured CUDA graph (0 = plain launches) */
     long long n_total;          /* particles over all replicas */
     long long neighbor_entries; /* sum of neighbour counts at the most recent build */
@@ -154,17 +156,33 @@ int md_get_forces(md_sim *sim, int replica, double *f, double *u, double *w);
  * prior md_step or md_get_forces (the list exists only after a build). */
 int md_get_neighbors(md_sim *sim, int replica, int max_per_particle, int *counts, int *nbrs);
 
-/* Kernel shape: tp in {1,2,4,8,16,32} threads per particle (Sec. 3 t_p), block threads per CTA
- * (multiple of 32, tp <= block <= 1024), reach in {1,2,3}: cell edge >= (rc_max + skin)/reach
- * with a (2 reach + 1)^3 stencil (Sec. 7 uses reach 2).  0 keeps the current value. */
-int md_set_tuning(md_sim *sim, int tp, int block, int reach);
-int md_get_tuning(md_sim *sim, int *tp, int *block, int *reach);
+/* Kernel shape: tp in {1,2,4,8,16,32} threads per particle in the force kernel (Sec. 3 t_p),
+ * block threads per CTA (multiple of 32, tp <= block <= 1024), reach in {1,2,3}: cell edge
+ * >= (rc_max + skin)/reach with a (2 reach + 1)^3 stencil (Sec. 7 uses reach 2), build_lanes in
+ * {1,2,4,8,16,32} lanes per particle in the list build (Sec. 7 uses one thread per particle;
+ * the list order, hence every result bit, does not depend on it).  0 keeps the current value. */
+int md_set_tuning(md_sim *sim, int tp, int block, int reach, int build_lanes);
+int md_get_tuning(md_sim *sim, int *tp, int *block, int *reach, int *build_lanes);
+
+/* Neighbour-list capacity per particle (Sec. 4: a fixed N x n_max array, doubled automatically
+ * when a build overflows).  The initial capacity is 1.35 x the ideal-gas count within
+ * rc_max + skin plus 24.  Reallocates the list and forces a rebuild of every replica. */
+int md_set_list_capacity(md_sim *sim, int n_max);
+
+/* Kernel path: 1 = grid kernels (one CTA per tile of any replica; the rebuild is a chain of
+ * kernels behind a CUDA-graph IF node), 2 = replica-resident kernel (persistent CTAs that each
+ * run a whole step of one replica at a time in shared memory, rebuild included; mixed precision,
+ * replicas up to the shared-memory limit), 0 = automatic (2 when it applies and there are at least
+ * 32 replicas).  Both paths give the same results bit for bit.  MD_EINVAL if 2 does not apply. */
+enum { MD_PATH_AUTO = 0, MD_PATH_GRID = 1, MD_PATH_REPLICA = 2 };
+int md_set_path(md_sim *sim, int path);
 
 /* Steps captured per CUDA graph replay (even, >= 2), or 0 for plain kernel launches with
  * device-side early exit of the rebuild kernels (the baseline launch mode). */
 int md_set_graph_block(md_sim *sim, int steps);
 
-/* Parameter search of the Appendix, reduced to tp, block and reach: short timed runs from the
+/* Parameter search of the Appendix, over the kernel path, tp, block, reach and build_lanes: short
+ * timed runs from the
  * current state (restored after every trial), single-minimum line searches with the break rules
  * of the Appendix.  cache_path (may be NULL) is a text file of tuned parameters keyed by the
  * user parameters and the GPU name; a hit skips the search.  The state is unchanged. */

@@ -10,8 +10,9 @@
 //   vel         : Real4 velocities v(t - dt/2), .w unused
 //   id          : user index inside the replica
 //   pos_build   : Real4 positions at the last list build (rebuild check, Sec. 6)
-//   nbl         : int32 neighbour slots, column-major: neighbour k of slot i at nbl[k*ncap + i]
-//                 (Sec. 5: first neighbours of all particles contiguous, then second, ...)
+//   nbl         : int32 neighbour slots, column-major within 32-particle slices: neighbour k of
+//                 slot i at ((i/32) * nmax + k) * 32 + i%32 (Sec. 5: first neighbours of the
+//                 particles contiguous, then second, ...; one slice per warp)
 //   nnb         : int32 neighbour counts
 #pragma once
 #include <cuda_runtime.h>
@@ -35,7 +36,14 @@ struct SysDesc {
     int span;              // cells visited per dimension (min(2 reach + 1, nc))
     double L, invL;
     float Lf, invLf, cell_scale, pad;  // cell_scale = nc / L rounded to float
+    float halfLf, Llo;     // (float)(L/2), L - (float)L rounded to float
     double K0;             // (3n - 3) T0 / 2
+};
+
+// Work list of one rebuild pass (written by k_plan): the replicas rebuilt and prefix sums of
+// their particle and cell counts (arrays plan_rep, plan_pp, plan_pc).
+struct Plan {
+    int nflag, tot_p, tot_c, pad;
 };
 
 // Per type-pair LJ table (shifted potential, Sec. 2).
@@ -67,8 +75,9 @@ struct Ctrl {
     unsigned int global_ticket;
     long long step;     // completed steps (all replicas step together)
     long long rebuild_passes;
-    unsigned long long nb_entries;  // sum of neighbour counts written by the last pass
-    int pad[2];
+    int q1, q2;         // replica queue cursors of the replica-resident kernel
+    int rep_overflow;   // a replica-resident build overflowed (results stay exact; grow n_max)
+    int pad;
 };
 
 template <typename R> struct StepArgs {
@@ -81,7 +90,7 @@ template <typename R> struct StepArgs {
     const V4 *pos_build;
     const int *nbl;
     const int *nnb;
-    long long ncap;           // column stride of nbl (= total slots)
+    int nmax;                 // list capacity per particle (slice stride)
     const int *tile_rep;      // tile -> replica
     const SysDesc *sys;
     const PairTab *tab;
@@ -92,7 +101,12 @@ template <typename R> struct StepArgs {
     Thermo *th;
     Ctrl *ctrl;
     int *moved;               // per replica: some particle moved > s/2 this step
-    int *need;                // per replica: rebuild before the next step
+    const int *need_in;       // per replica: rebuild before this step (read)
+    int *need_out;            // per replica: rebuild before the next step (written)
+    int *id_g;                // user ids (the replica-resident kernel permutes them)
+    const int *rep_order;     // replicas by descending size (replica-resident queue)
+    int rep_nmax, rep_cmax;   // largest replica and cell count (shared-memory sizing)
+    int tile_threads;         // threads per tile (the grid kernel's block size)
     unsigned int *rep_ticket; // per replica tile tickets
     double *partial;          // per tile MD_NRED partial sums
     double *log;              // MD_LOG_COLS doubles per (row, replica) or null
@@ -132,15 +146,18 @@ template <typename R> struct RebuildArgs {
     const int *crep;         // cell -> replica
     int *nbl;
     int *nnb;
-    long long ncap;
     int nmax;
+    Plan *plan;
+    int *plan_rep, *plan_pp, *plan_pc;
+    int nsm;                 // SMs, for the persistent grids
+    int tpb;                 // lanes per particle in the list build
     const SysDesc *sys;
     const PairTab *tab;
     int ntypes;
     int nrep;
     int ntot;
     int ctot;
-    const int *need;
+    const int *need_in;
     Ctrl *ctrl;
     Thermo *th;
 };
@@ -152,3 +169,17 @@ template <typename R> cudaError_t launch_rebuild(const RebuildArgs<R> &a, cudaSt
 template <typename R> cudaError_t launch_rebuild_timed(const RebuildArgs<R> &a, cudaStream_t s,
                                                        cudaEvent_t e0, cudaEvent_t e1);
 cudaError_t launch_arm(const Ctrl *ctrl, cudaGraphConditionalHandle h, cudaStream_t s);
+// Replica-resident step kernel (FP32 / mixed precision only).
+cudaError_t launch_rep(const StepArgs<float> &a, const RebuildArgs<float> &b, int tp, int block,
+                       int grid, size_t smem, cudaStream_t s);
+cudaError_t prepare_rep(int tp, int tpb, bool single, size_t smem);
+// Dynamic shared memory of the replica-resident kernel for replicas of up to nmax particles and
+// cmax cells with `block` threads and tp threads per particle.
+inline size_t rep_smem_bytes(int nmax, int cmax, int block, int tp, int cta_threads) {
+    const int P = block / tp;
+    // tile partials, rounded up to whole rounds of cta_threads / block tiles
+    const size_t per_round = (size_t)(cta_threads / block);
+    const size_t tiles = (((size_t)(nmax + P - 1) / P + per_round - 1) / per_round) * per_round;
+    return (size_t)nmax * 16 + (size_t)(2 * cmax + 1) * 4 + (size_t)2 * nmax * 4 + 16 +
+           tiles * MD_NRED * 8;
+}

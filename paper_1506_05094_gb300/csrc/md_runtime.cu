@@ -32,6 +32,8 @@ struct Buffers {
     int *cell_of = nullptr, *rank = nullptr, *perm = nullptr;
     int *cell_start = nullptr, *count = nullptr, *crep = nullptr, *prep = nullptr;
     int *nbl = nullptr, *nnb = nullptr;
+    Plan *plan = nullptr;
+    int *plan_arr = nullptr;
     SysDesc *sys = nullptr;
     PairTab *tab = nullptr;
     Thermo *th = nullptr;
@@ -58,7 +60,14 @@ struct md_sim {
     double skin = 0.3, rc_max = 0.0;
     int integrator = MD_NVE_LEAPFROG;
     double dt = 0.005, T0 = 1.0, tau = 0.2;
-    int tp = 1, block = 128, reach = 2;
+    int tp = 1, block = 128, reach = 2, tpb = 8;
+    int path = 0;            // 0 auto, 1 grid, 2 replica-resident
+    bool rep_ok = false;     // replica-resident kernel usable with the current shape
+    size_t rep_smem = 0;
+    int rep_threads = 512, rep_ctas = 1;
+    int rep_nmax = 0, rep_cmax = 0;
+    int *rep_order = nullptr;
+    int nsm = 148;
     int graph_block = 100;
     int nmax = 0;
     int log_cap = 0;
@@ -195,6 +204,25 @@ int configure_layout(md_sim *s, bool realloc_cells) {
             dalloc(s, &s->b.partial, (size_t)ntiles * MD_NRED))
             return MD_ENOMEM;
     }
+    // replica-resident kernel: shared memory for the largest replica
+    s->rep_nmax = 0;
+    s->rep_cmax = 0;
+    for (int r = 0; r < s->R; ++r) {
+        s->rep_nmax = std::max(s->rep_nmax, s->sys[r].n);
+        s->rep_cmax = std::max(s->rep_cmax, s->sys[r].nc * s->sys[r].nc * s->sys[r].nc);
+    }
+    s->rep_threads = std::max(s->block, 512);
+    s->rep_smem = rep_smem_bytes(s->rep_nmax, s->rep_cmax, s->block, s->tp, s->rep_threads);
+    int optin = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
+    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, s->device);
+    // resident CTAs per SM: shared memory (plus ~8 KB static) and 64 registers x threads
+    s->rep_ctas = std::max(1, std::min(per_sm / (int)(s->rep_smem + 8192),
+                                       65536 / (64 * s->rep_threads)));
+    s->rep_ok = s->precision == MD_MIXED && s->rep_smem + 8192 <= (size_t)optin &&
+                (s->tpb == 8 || s->tpb == 32) &&
+                prepare_rep(s->tp, s->tpb, s->nt == 1, s->rep_smem) == cudaSuccess;
+    cudaGetLastError();
     std::vector<int> tr(ntiles);
     for (int r = 0; r < s->R; ++r)
         for (int t = 0; t < s->sys[r].ntiles; ++t) tr[s->sys[r].tile_off + t] = r;
@@ -206,15 +234,20 @@ int configure_layout(md_sim *s, bool realloc_cells) {
     return MD_OK;
 }
 
+// sliced layout: ceil(ntot / 32) slices of nmax x 32 entries
+size_t nbl_entries(const md_sim *s) { return (((size_t)s->ntot + 31) / 32) * 32 * (size_t)s->nmax; }
+
 int alloc_nbl(md_sim *s) {
     dfree(s->b.nbl);
-    return dalloc(s, &s->b.nbl, (size_t)s->ntot * (size_t)s->nmax);
+    return dalloc(s, &s->b.nbl, nbl_entries(s));
 }
 
 // Force a full rebuild of every replica before the next step (device flags, stream-ordered).
+int *need_now(md_sim *s) { return s->b.need + (size_t)(s->h_step & 1) * s->R; }
+
 int request_rebuild_all(md_sim *s) {
     std::vector<int> ones(s->R, 1);
-    if (cudaMemcpyAsync(s->b.need, ones.data(), sizeof(int) * s->R, cudaMemcpyHostToDevice,
+    if (cudaMemcpyAsync(need_now(s), ones.data(), sizeof(int) * s->R, cudaMemcpyHostToDevice,
                         s->stream) != cudaSuccess)
         return fail(s, MD_ECUDA);
     const int one = 1;
@@ -237,7 +270,7 @@ template <typename R> StepArgs<R> step_args(md_sim *s, int parity, int force_onl
     a.pos_build = (const V4 *)s->b.pos_build;
     a.nbl = s->b.nbl;
     a.nnb = s->b.nnb;
-    a.ncap = s->ntot;
+    a.nmax = s->nmax;
     a.tile_rep = s->b.tile_rep;
     a.sys = s->b.sys;
     a.tab = s->b.tab;
@@ -250,7 +283,13 @@ template <typename R> StepArgs<R> step_args(md_sim *s, int parity, int force_onl
     a.th = s->b.th;
     a.ctrl = s->b.ctrl;
     a.moved = s->b.moved;
-    a.need = s->b.need;
+    a.need_in = s->b.need + (size_t)parity * s->R;
+    a.need_out = s->b.need + (size_t)(parity ^ 1) * s->R;
+    a.id_g = s->b.id;
+    a.rep_order = s->rep_order;
+    a.rep_nmax = s->rep_nmax;
+    a.rep_cmax = s->rep_cmax;
+    a.tile_threads = s->block;
     a.rep_ticket = s->b.ticket;
     a.partial = s->b.partial;
     a.log = s->b.log;
@@ -294,15 +333,20 @@ template <typename R> RebuildArgs<R> rebuild_args(md_sim *s, int parity, const v
     a.crep = s->b.crep;
     a.nbl = s->b.nbl;
     a.nnb = s->b.nnb;
-    a.ncap = s->ntot;
     a.nmax = s->nmax;
+    a.plan = s->b.plan;
+    a.plan_rep = s->b.plan_arr;
+    a.plan_pp = s->b.plan_arr + s->R;
+    a.plan_pc = s->b.plan_arr + 2 * s->R + 1;
+    a.nsm = s->nsm;
+    a.tpb = s->tpb;
     a.sys = s->b.sys;
     a.tab = s->b.tab;
     a.ntypes = s->nt;
     a.nrep = s->R;
     a.ntot = s->ntot;
     a.ctot = s->ctot;
-    a.need = s->b.need;
+    a.need_in = s->b.need + (size_t)parity * s->R;
     a.ctrl = s->b.ctrl;
     a.th = s->b.th;
     return a;
@@ -313,8 +357,22 @@ cudaError_t do_rebuild(md_sim *s, int parity, cudaStream_t st, const void *key =
     return launch_rebuild<float>(rebuild_args<float>(s, parity, key), st);
 }
 
+bool use_rep(const md_sim *s) {
+    if (!s->rep_ok) return false;
+    if (s->path == 2) return true;
+    if (s->path == 1) return false;
+    return s->R >= 32;   // auto: enough replicas to occupy every SM with whole replicas
+}
+
 cudaError_t do_step(md_sim *s, int parity, cudaStream_t st, int force_only,
                     cudaGraphConditionalHandle next = 0, int has_next = 0) {
+    if (!force_only && use_rep(s)) {
+        StepArgs<float> a = step_args<float>(s, parity, 0);
+        a.has_next = 0;
+        RebuildArgs<float> b = rebuild_args<float>(s, parity, nullptr);
+        const int grid = std::min(s->R, s->rep_ctas * s->nsm);
+        return launch_rep(a, b, s->tp, s->rep_threads, grid, s->rep_smem, st);
+    }
     if (s->precision == MD_FP64) {
         StepArgs<double> a = step_args<double>(s, parity, force_only);
         a.next_handle = next;
@@ -331,6 +389,28 @@ cudaError_t do_step(md_sim *s, int parity, cudaStream_t st, int force_only,
 int build_graph(md_sim *s, int p) {
     const int B = s->graph_block;
     cudaGraph_t g = nullptr;
+    if (use_rep(s)) {   // one replica-resident launch per step: the rebuild is inside the kernel
+        if (cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return fail(s, MD_ECUDA);
+        bool okr = true;
+        for (int k = 0; okr && k < B; ++k) okr = do_step(s, (p + k) & 1, s->cap_stream, 0) == cudaSuccess;
+        cudaGraph_t outg = nullptr;
+        cudaError_t ee = cudaStreamEndCapture(s->cap_stream, &outg);
+        if (!okr || ee != cudaSuccess || !outg) {
+            if (outg) cudaGraphDestroy(outg);
+            cudaGetLastError();
+            return fail(s, MD_ECUDA);
+        }
+        cudaGraphExec_t exr = nullptr;
+        if (cudaGraphInstantiate(&exr, outg, 0) != cudaSuccess) {
+            cudaGraphDestroy(outg);
+            return fail(s, MD_ECUDA);
+        }
+        s->graph[p] = outg;
+        s->exec[p] = exr;
+        s->graph_len[p] = B;
+        return MD_OK;
+    }
     if (cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
         return fail(s, MD_ECUDA);
     cudaStreamCaptureStatus st;
@@ -409,6 +489,21 @@ int recover_overflow(md_sim *s) {
     if (cudaMemcpyAsync(s->b.ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, s->stream) !=
             cudaSuccess ||
         cudaMemsetAsync(s->b.ticket, 0, sizeof(unsigned) * s->R, s->stream) != cudaSuccess)
+        return fail(s, MD_ECUDA);
+    s->overflows++;
+    return request_rebuild_all(s);
+}
+
+int grow_after_rep_overflow(md_sim *s) {
+    const int seen = s->h_ctrl->max_count;
+    s->nmax = std::max(2 * s->nmax, seen + seen / 4 + 8);
+    destroy_graphs(s);
+    if (alloc_nbl(s)) return MD_ENOMEM;
+    Ctrl c = *s->h_ctrl;
+    c.rep_overflow = 0;
+    c.max_count = 0;
+    if (cudaMemcpyAsync(s->b.ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, s->stream) !=
+        cudaSuccess)
         return fail(s, MD_ECUDA);
     s->overflows++;
     return request_rebuild_all(s);
@@ -496,7 +591,8 @@ void md_destroy(md_sim *s) {
                      (void **)&b.txd, (void **)&b.tyd, (void **)&b.tzd, &b.tvel, (void **)&b.timg,
                      (void **)&b.tid, (void **)&b.cell_of, (void **)&b.rank, (void **)&b.perm,
                      (void **)&b.cell_start, (void **)&b.count, (void **)&b.crep,
-                     (void **)&b.prep, (void **)&b.nbl, (void **)&b.nnb, (void **)&b.sys,
+                     (void **)&b.prep, (void **)&b.nbl, (void **)&b.nnb, (void **)&b.plan,
+                     (void **)&b.plan_arr, (void **)&b.sys,
                      (void **)&b.tab, (void **)&b.th, (void **)&b.ctrl, (void **)&b.moved,
                      (void **)&b.need, (void **)&b.ticket, (void **)&b.partial,
                      (void **)&b.tile_rep, (void **)&b.log, &b.f_out, &b.w_out};
@@ -504,6 +600,7 @@ void md_destroy(md_sim *s) {
         if (*p) cudaFree(*p);
         *p = nullptr;
     }
+    if (s->rep_order) cudaFree(s->rep_order);
     if (s->h_ctrl) cudaFreeHost(s->h_ctrl);
     for (cudaEvent_t &e : s->ev)
         if (e) cudaEventDestroy(e);
@@ -546,6 +643,11 @@ int md_create(md_sim **out, int n_replicas, const int *n_particles, const double
     md_sim *s = new (std::nothrow) md_sim();
     if (!s) return MD_ENOMEM;
     cudaGetDevice(&s->device);
+    if (cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess ||
+        s->nsm < 1) {
+        cudaGetLastError();
+        s->nsm = 148;
+    }
     s->R = n_replicas;
     s->nt = n_types;
     s->precision = precision;
@@ -592,6 +694,8 @@ int md_create(md_sim **out, int n_replicas, const int *n_particles, const double
         d.invL = 1.0 / box[r];
         d.Lf = (float)box[r];
         d.invLf = (float)(1.0 / box[r]);
+        d.halfLf = (float)(0.5 * box[r]);
+        d.Llo = (float)(box[r] - (double)d.Lf);
         d.K0 = 0.5 * (3.0 * d.n - 3.0) * s->T0;
         s->off[r] = off;
         off += d.n;
@@ -627,12 +731,14 @@ int md_create(md_sim **out, int n_replicas, const int *n_particles, const double
     rc |= dalloc(s, &b.cell_of, N); rc |= dalloc(s, &b.rank, N); rc |= dalloc(s, &b.perm, N);
     rc |= dalloc(s, &b.prep, N);
     rc |= dalloc(s, &b.nnb, N);
+    rc |= dalloc(s, &b.plan, 1);
+    rc |= dalloc(s, &b.plan_arr, 3 * (size_t)n_replicas + 2);
     rc |= dalloc(s, &b.sys, n_replicas);
     rc |= dalloc(s, &b.tab, MD_MAX_PAIRS);
     rc |= dalloc(s, &b.th, n_replicas);
     rc |= dalloc(s, &b.ctrl, 1);
     rc |= dalloc(s, &b.moved, n_replicas);
-    rc |= dalloc(s, &b.need, n_replicas);
+    rc |= dalloc(s, &b.need, 2 * (size_t)n_replicas);   // by step parity: read / written
     rc |= dalloc(s, &b.ticket, n_replicas);
     rc |= dallocb(s, &b.f_out, N * R4);
     rc |= dallocb(s, &b.w_out, N * (R4 / 4));
@@ -646,15 +752,24 @@ int md_create(md_sim **out, int n_replicas, const int *n_particles, const double
     std::vector<int> prep(N);
     for (int r = 0; r < n_replicas; ++r)
         for (int k = 0; k < s->n[r]; ++k) prep[s->off[r] + k] = r;
+    // replica queue of the replica-resident kernel: descending size (largest jobs first)
+    std::vector<int> order(n_replicas);
+    for (int r = 0; r < n_replicas; ++r) order[r] = r;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return s->n[x] > s->n[y]; });
+    if (dalloc(s, &s->rep_order, n_replicas)) { md_destroy(s); return MD_ENOMEM; }
     bool ok = cudaMemcpy(b.prep, prep.data(), N * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemcpy(s->rep_order, order.data(), n_replicas * sizeof(int),
+                          cudaMemcpyHostToDevice) == cudaSuccess;
     ok = ok && cudaMemcpy(b.tab, s->tab.data(), sizeof(PairTab) * MD_MAX_PAIRS,
                           cudaMemcpyHostToDevice) == cudaSuccess;
     ok = ok && cudaMemset(b.th, 0, sizeof(Thermo) * n_replicas) == cudaSuccess;
     ok = ok && cudaMemset(b.ctrl, 0, sizeof(Ctrl)) == cudaSuccess;
     ok = ok && cudaMemset(b.moved, 0, sizeof(int) * n_replicas) == cudaSuccess;
-    ok = ok && cudaMemset(b.need, 0, sizeof(int) * n_replicas) == cudaSuccess;
+    ok = ok && cudaMemset(b.need, 0, sizeof(int) * 2 * n_replicas) == cudaSuccess;
     ok = ok && cudaMemset(b.ticket, 0, sizeof(unsigned) * n_replicas) == cudaSuccess;
     ok = ok && cudaMemset(b.nnb, 0, sizeof(int) * N) == cudaSuccess;
+    ok = ok && cudaMemset(b.plan, 0, sizeof(Plan)) == cudaSuccess;
     ok = ok && cudaMemset(b.img, 0, sizeof(int4) * N) == cudaSuccess;
     ok = ok && cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) == cudaSuccess;
     s->own_stream = ok;
@@ -764,7 +879,7 @@ int md_set_state(md_sim *s, int r, const double *pos, const int *type, const dou
     ok = ok && cudaMemcpy(b.id + o, ids.data(), n * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
     ok = ok && cudaMemset(b.nnb + o, 0, n * sizeof(int)) == cudaSuccess;
     ok = ok && cudaMemcpy(b.th + r, &th, sizeof(th), cudaMemcpyHostToDevice) == cudaSuccess;
-    ok = ok && cudaMemcpy(b.need + r, &one, sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemcpy(need_now(s) + r, &one, sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
     ok = ok && cudaMemcpy(b.moved + r, &zero, sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
     ok = ok && cudaMemcpy(&b.ctrl->need_any, &one, sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
     if (!ok) return fail(s, MD_ECUDA);
@@ -798,7 +913,7 @@ int md_step(md_sim *s, long long n_steps) {
                 s->h_step += s->graph_block;
                 remaining -= s->graph_block;
             } else {
-                if (do_rebuild(s, p, s->stream) != cudaSuccess ||
+                if ((!use_rep(s) && do_rebuild(s, p, s->stream) != cudaSuccess) ||
                     do_step(s, p, s->stream, 0) != cudaSuccess)
                     return fail(s, MD_ECUDA);
                 s->h_step += 1;
@@ -819,6 +934,10 @@ int md_step(md_sim *s, long long n_steps) {
             continue;
         }
         if (s->h_ctrl->step != s->h_step) return fail(s, MD_ECUDA);
+        if (s->h_ctrl->rep_overflow) {
+            // replica-resident builds that overflowed used list-free forces (exact); grow n_max
+            if ((rc = grow_after_rep_overflow(s))) return rc;
+        }
     }
     return MD_OK;
 }
@@ -943,20 +1062,23 @@ int md_get_neighbors(md_sim *s, int r, int maxp, int *counts, int *nbrs) {
     if (!counts || maxp < 0 || (maxp > 0 && !nbrs)) return MD_EINVAL;
     if (s->sticky) return s->sticky;
     const int n = s->n[r], o = s->off[r];
-    std::vector<int> cnt(n), ids(n), lst((size_t)n * s->nmax);
+    const int sl0 = o / 32, sl1 = (o + n - 1) / 32;            // slices holding the replica
+    const size_t per = (size_t)32 * s->nmax;
+    std::vector<int> cnt(n), ids(n), lst((size_t)(sl1 - sl0 + 1) * per);
     if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(s, MD_ECUDA);
     bool ok = cudaMemcpy(cnt.data(), s->b.nnb + o, n * sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess;
     ok = ok && cudaMemcpy(ids.data(), s->b.id + o, n * sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess;
-    ok = ok && cudaMemcpy2D(lst.data(), n * sizeof(int), s->b.nbl + o, (size_t)s->ntot * sizeof(int),
-                            n * sizeof(int), s->nmax, cudaMemcpyDeviceToHost) == cudaSuccess;
+    ok = ok && cudaMemcpy(lst.data(), s->b.nbl + (size_t)sl0 * per, lst.size() * sizeof(int),
+                          cudaMemcpyDeviceToHost) == cudaSuccess;
     if (!ok) return fail(s, MD_ECUDA);
     for (int k = 0; k < n; ++k) {
-        const int q = ids[k];
+        const int q = ids[k], i = o + k;
         counts[q] = cnt[k];
         for (int m = 0; m < maxp; ++m) {
             int v = -1;
             if (m < cnt[k] && m < s->nmax) {
-                const int j = lst[(size_t)m * n + k] - o;
+                const size_t off = (((size_t)(i / 32 - sl0) * s->nmax + m) * 32) + (i % 32);
+                const int j = lst[off] - o;
                 v = (j >= 0 && j < n) ? ids[j] : -2;
             }
             nbrs[(size_t)q * maxp + m] = v;
@@ -965,17 +1087,20 @@ int md_get_neighbors(md_sim *s, int r, int maxp, int *counts, int *nbrs) {
     return MD_OK;
 }
 
-int md_set_tuning(md_sim *s, int tp, int block, int reach) {
+int md_set_tuning(md_sim *s, int tp, int block, int reach, int build_lanes) {
     if (!s) return MD_EINVAL;
     if (s->sticky) return s->sticky;
     const int ntp = tp ? tp : s->tp, nb = block ? block : s->block, nr = reach ? reach : s->reach;
-    if (!is_pow2_tp(ntp) || nb < 32 || nb > 1024 || (nb % 32) != 0 || nb < ntp || nr < 1 || nr > 3)
+    const int nl = build_lanes ? build_lanes : s->tpb;
+    if (!is_pow2_tp(ntp) || nb < 32 || nb > 1024 || (nb % 32) != 0 || nb < ntp || nr < 1 ||
+        nr > 3 || !is_pow2_tp(nl))
         return MD_EINVAL;
     if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(s, MD_ECUDA);
     const bool cells_change = nr != s->reach;
     s->tp = ntp;
     s->block = nb;
     s->reach = nr;
+    s->tpb = nl;
     destroy_graphs(s);
     int rc = configure_layout(s, cells_change);
     if (rc) return rc == MD_ENOMEM ? MD_ENOMEM : fail(s, MD_ECUDA);
@@ -983,11 +1108,32 @@ int md_set_tuning(md_sim *s, int tp, int block, int reach) {
     return MD_OK;
 }
 
-int md_get_tuning(md_sim *s, int *tp, int *block, int *reach) {
+int md_get_tuning(md_sim *s, int *tp, int *block, int *reach, int *build_lanes) {
     if (!s) return MD_EINVAL;
     if (tp) *tp = s->tp;
     if (block) *block = s->block;
     if (reach) *reach = s->reach;
+    if (build_lanes) *build_lanes = s->tpb;
+    return MD_OK;
+}
+
+int md_set_list_capacity(md_sim *s, int n_max) {
+    if (!s || n_max < 1) return MD_EINVAL;
+    if (s->sticky) return s->sticky;
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(s, MD_ECUDA);
+    destroy_graphs(s);
+    s->nmax = n_max;
+    if (alloc_nbl(s)) return MD_ENOMEM;
+    return request_rebuild_all(s);
+}
+
+int md_set_path(md_sim *s, int path) {
+    if (!s || path < 0 || path > 2) return MD_EINVAL;
+    if (s->sticky) return s->sticky;
+    if (path == 2 && !s->rep_ok) return MD_EINVAL;
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(s, MD_ECUDA);
+    destroy_graphs(s);
+    s->path = path;
     return MD_OK;
 }
 
@@ -1025,6 +1171,8 @@ int md_get_stats(md_sim *s, md_stats *out) {
     out->tp = s->tp;
     out->block = s->block;
     out->reach = s->reach;
+    out->build_lanes = s->tpb;
+    out->path = use_rep(s) ? 2 : 1;
     out->graph_block = s->graph_block;
     out->n_total = s->ntot;
     out->neighbor_entries = ent;
@@ -1043,10 +1191,15 @@ int md_profile(md_sim *s, int n_steps, md_timing *out) {
     for (int k = 0; k < n_steps; ++k) {
         int rc = read_ctrl(s);
         if (rc) return rc;
-        const bool will = s->h_ctrl->need_any && !s->h_ctrl->halt;
+        const bool will = s->h_ctrl->need_any && !s->h_ctrl->halt && !use_rep(s);
         const int p = (int)(s->h_step & 1);
         cudaError_t e;
-        if (s->precision == MD_FP64)
+        if (use_rep(s))
+            e = cudaEventRecord(s->ev[0], s->stream) == cudaSuccess &&
+                        cudaEventRecord(s->ev[1], s->stream) == cudaSuccess
+                    ? cudaSuccess
+                    : cudaErrorUnknown;
+        else if (s->precision == MD_FP64)
             e = launch_rebuild_timed<double>(rebuild_args<double>(s, p, nullptr), s->stream, s->ev[0], s->ev[1]);
         else
             e = launch_rebuild_timed<float>(rebuild_args<float>(s, p, nullptr), s->stream, s->ev[0], s->ev[1]);
@@ -1060,6 +1213,7 @@ int md_profile(md_sim *s, int n_steps, md_timing *out) {
             --k;
             continue;
         }
+        if (s->h_ctrl->rep_overflow && (rc = grow_after_rep_overflow(s))) return rc;
         float a = 0.f, c = 0.f;
         cudaEventElapsedTime(&a, s->ev[0], s->ev[1]);
         cudaEventElapsedTime(&c, s->ev[1], s->ev[2]);
@@ -1163,7 +1317,8 @@ int md_save_checkpoint(md_sim *s, void *buf, size_t bytes) {
     ok = ok && cudaMemcpy(vel.data(), b.vel, N * R4, cudaMemcpyDeviceToHost) == cudaSuccess;
     ok = ok && cudaMemcpy(pb.data(), b.pos_build, N * R4, cudaMemcpyDeviceToHost) == cudaSuccess;
     ok = ok && cudaMemcpy(th.data(), b.th, sizeof(Thermo) * s->R, cudaMemcpyDeviceToHost) == cudaSuccess;
-    ok = ok && cudaMemcpy(need.data(), b.need, sizeof(int) * s->R, cudaMemcpyDeviceToHost) == cudaSuccess;
+    ok = ok && cudaMemcpy(need.data(), b.need + (size_t)(s->h_step & 1) * s->R, sizeof(int) * s->R,
+                          cudaMemcpyDeviceToHost) == cudaSuccess;
     if (!ok) return fail(s, MD_ECUDA);
     unsigned char *p = (unsigned char *)buf;
     CkHeader h;
@@ -1286,7 +1441,7 @@ int md_load_checkpoint(md_sim *s, const void *buf, size_t bytes) {
     // pending rebuild flags as saved
     int any = 0;
     for (int v : need) any |= v;
-    ok = cudaMemcpy(b.need, need.data(), sizeof(int) * s->R, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = cudaMemcpy(need_now(s), need.data(), sizeof(int) * s->R, cudaMemcpyHostToDevice) == cudaSuccess;
     ok = ok && cudaMemcpy(&b.ctrl->need_any, &any, sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
     if (!ok) return fail(s, MD_ECUDA);
     destroy_graphs(s);
@@ -1336,7 +1491,8 @@ std::string tune_key(md_sim *s) {
     return k;
 }
 
-bool cache_lookup(const char *path, const std::string &key, int *tp, int *block, int *reach) {
+bool cache_lookup(const char *path, const std::string &key, int *tp, int *block, int *reach,
+                  int *lanes) {
     if (!path) return false;
     FILE *f = std::fopen(path, "r");
     if (!f) return false;
@@ -1344,9 +1500,9 @@ bool cache_lookup(const char *path, const std::string &key, int *tp, int *block,
     bool found = false;
     while (std::fgets(line, sizeof(line), f)) {
         char k[900];
-        int a, b, c;
-        if (std::sscanf(line, "%899s %d %d %d", k, &a, &b, &c) == 4 && key == k) {
-            *tp = a; *block = b; *reach = c;
+        int a, b, c, d;
+        if (std::sscanf(line, "%899s %d %d %d %d", k, &a, &b, &c, &d) == 5 && key == k) {
+            *tp = a; *block = b; *reach = c; *lanes = d;
             found = true;   // the last entry for a key wins
         }
     }
@@ -1354,11 +1510,12 @@ bool cache_lookup(const char *path, const std::string &key, int *tp, int *block,
     return found;
 }
 
-void cache_store(const char *path, const std::string &key, int tp, int block, int reach, double ms) {
+void cache_store(const char *path, const std::string &key, int tp, int block, int reach, int lanes,
+                 double ms) {
     if (!path) return;
     FILE *f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "%s %d %d %d %.6f\n", key.c_str(), tp, block, reach, ms);
+    std::fprintf(f, "%s %d %d %d %d %.6f\n", key.c_str(), tp, block, reach, lanes, ms);
     std::fclose(f);
 }
 
@@ -1370,22 +1527,25 @@ extern "C" int md_autotune(md_sim *s, const char *cache_path, int steps) {
     for (char c : s->loaded)
         if (!c) return MD_ESTATE;
     const std::string key = tune_key(s);
-    int tp = 0, block = 0, reach = 0;
-    if (cache_lookup(cache_path, key, &tp, &block, &reach) && is_pow2_tp(tp) && block >= tp &&
-        block <= 1024 && block % 32 == 0 && reach >= 1 && reach <= 3)
-        return md_set_tuning(s, tp, block, reach);
+    int tp = 0, block = 0, reach = 0, lanes = 0;
+    if (cache_lookup(cache_path, key, &tp, &block, &reach, &lanes) && is_pow2_tp(tp) &&
+        block >= tp && block <= 1024 && block % 32 == 0 && reach >= 1 && reach <= 3 &&
+        is_pow2_tp(lanes / 10) && lanes % 10 <= 2) {
+        int e = md_set_tuning(s, tp, block, reach, lanes / 10);
+        if (e) return e;
+        return md_set_path(s, (lanes % 10 == 2 && s->rep_ok) ? 2 : 1);
+    }
     size_t bytes = 0;
     md_checkpoint_size(s, &bytes);
     std::vector<unsigned char> ck(bytes);
     int rc = md_save_checkpoint(s, ck.data(), bytes);
     if (rc) return rc;
     const int gb_saved = s->graph_block;
-    const int gb = (steps >= 4) ? (steps / 2) * 2 : 2;
-    int trial_block = std::min(gb, 50);
-    if (trial_block & 1) --trial_block;
+    int trial_block = std::min((steps / 2) * 2, 50);
+    if (trial_block < 2) trial_block = 2;
     // time one configuration: restore, warm up (graph capture + first rebuild), restore, time
-    auto trial = [&](int t, int b, int re, double *ms) -> int {
-        int e = md_set_tuning(s, t, b, re);
+    auto trial = [&](int t, int b, int re, int la, double *ms) -> int {
+        int e = md_set_tuning(s, t, b, re, la);
         if (e) return e;
         if ((e = md_set_graph_block(s, trial_block))) return e;
         if ((e = md_load_checkpoint(s, ck.data(), bytes))) return e;
@@ -1405,14 +1565,25 @@ extern "C" int md_autotune(md_sim *s, const char *cache_path, int steps) {
     for (int v : s->n) nmax_part = std::max(nmax_part, v);
     // Appendix defaults: t_p = 4 (p_b = 32) up to 10^4 particles, else t_p = 1 (p_b = 64)
     int best_tp = nmax_part <= 10000 ? 4 : 1, best_block = nmax_part <= 10000 ? 128 : 64;
-    int best_reach = 2;
+    int best_reach = 2, best_lanes = 8;
     double best = 1e30, t = 0.0;
-    // phase I: stencil reach at default kernel shape
+    // phase 0: grid path or replica-resident path (when both apply)
+    const int path_saved = s->path;
+    if (s->rep_ok) {
+        double tg = 0.0, tr = 0.0;
+        s->path = 1;
+        if ((rc = trial(best_tp, best_block, best_reach, best_lanes, &tg))) return rc;
+        s->path = 2;
+        if ((rc = trial(best_tp, best_block, best_reach, best_lanes, &tr))) return rc;
+        s->path = tr < tg ? 2 : 1;
+        best = std::min(tg, tr);
+    }
+    // phase I: cell stencil reach at the default kernel shape
     for (int re : {2, 1, 3}) {
-        if ((rc = trial(best_tp, best_block, re, &t))) return rc;
+        if ((rc = trial(best_tp, best_block, re, best_lanes, &t))) return rc;
         if (t < best) { best = t; best_reach = re; }
     }
-    // phase II: block size x threads per particle
+    // phase II: block size x threads per particle with the break rules of the Appendix
     const int blocks[] = {64, 128, 256, 512};
     for (int b : blocks) {
         double best_b = 1e30;
@@ -1420,16 +1591,29 @@ extern "C" int md_autotune(md_sim *s, const char *cache_path, int steps) {
         for (int tpv = 1; tpv <= 32; tpv *= 2) {
             if (tpv > b) break;
             if (nmax_part > 100000 && tpv > 1) break;   // Appendix: only t_p = 1 for N > 1e5
-            if ((rc = trial(tpv, b, best_reach, &t))) return rc;
+            if ((rc = trial(tpv, b, best_reach, best_lanes, &t))) return rc;
             if (t < best_b) best_b = t;
             if (t < best) { best = t; best_tp = tpv; best_block = b; worse = 0; continue; }
             if (t > 1.05 * best || ++worse >= 3) break;
         }
         if (best_b >= 1.10 * best) break;
     }
-    if ((rc = md_set_tuning(s, best_tp, best_block, best_reach))) return rc;
+    // phase III: lanes per particle of the list build (single minimum: walk down, then up);
+    // the replica-resident kernel is built for 8 and 32 lanes
+    for (int dir : {-1, 1}) {
+        int la = best_lanes;
+        for (;;) {
+            la = dir < 0 ? la / 2 : la * 2;
+            if (la < 1 || la > 32) break;
+            if (s->path == 2 && la != 8 && la != 32) continue;
+            if ((rc = trial(best_tp, best_block, best_reach, la, &t))) return rc;
+            if (t < best) { best = t; best_lanes = la; } else break;
+        }
+    }
+    if ((rc = md_set_tuning(s, best_tp, best_block, best_reach, best_lanes))) return rc;
     if ((rc = md_set_graph_block(s, gb_saved))) return rc;
     if ((rc = md_load_checkpoint(s, ck.data(), bytes))) return rc;
-    cache_store(cache_path, key, best_tp, best_block, best_reach, best);
+    (void)path_saved;
+    cache_store(cache_path, key, best_tp, best_block, best_reach, best_lanes * 10 + s->path, best);
     return MD_OK;
 }

@@ -25,7 +25,8 @@ LOG_COLS = ("step", "U", "W", "K_minus", "K_plus", "xi", "xi_int", "H", "px", "p
 # every function declared in include/md.h
 SYMBOLS = ("md_create", "md_set_integrator", "md_set_state", "md_set_stream", "md_step",
            "md_sync", "md_get_state", "md_get_energies", "md_get_forces", "md_get_neighbors",
-           "md_set_tuning", "md_get_tuning", "md_set_graph_block", "md_autotune",
+           "md_set_tuning", "md_get_tuning", "md_set_list_capacity", "md_set_path",
+           "md_set_graph_block", "md_autotune",
            "md_get_stats", "md_profile", "md_set_log", "md_get_log", "md_checkpoint_size",
            "md_save_checkpoint", "md_load_checkpoint", "md_destroy", "md_strerror")
 
@@ -46,7 +47,8 @@ class md_stats(C.Structure):
     _fields_ = [("steps", C.c_longlong), ("rebuild_passes", C.c_longlong),
                 ("replica_rebuilds", C.c_longlong), ("overflows", C.c_longlong),
                 ("n_max", C.c_int), ("max_neighbors", C.c_int), ("tp", C.c_int),
-                ("block", C.c_int), ("reach", C.c_int), ("graph_block", C.c_int),
+                ("block", C.c_int), ("reach", C.c_int), ("build_lanes", C.c_int),
+                ("path", C.c_int), ("graph_block", C.c_int),
                 ("n_total", C.c_longlong), ("neighbor_entries", C.c_longlong)]
 
 
@@ -87,8 +89,10 @@ def lib():
         "md_get_energies": [p, i, C.POINTER(md_energies)],
         "md_get_forces": [p, i, pd, pd, pd],
         "md_get_neighbors": [p, i, i, pi, pi],
-        "md_set_tuning": [p, i, i, i],
-        "md_get_tuning": [p, pi, pi, pi],
+        "md_set_tuning": [p, i, i, i, i],
+        "md_get_tuning": [p, pi, pi, pi, pi],
+        "md_set_list_capacity": [p, i],
+        "md_set_path": [p, i],
         "md_set_graph_block": [p, i],
         "md_autotune": [p, C.c_char_p, i],
         "md_get_stats": [p, C.POINTER(md_stats)],
@@ -207,13 +211,24 @@ class Sim:
     def set_stream(self, stream_handle: int):
         _ck(lib().md_set_stream(self._h, C.c_void_p(int(stream_handle))), "md_set_stream")
 
-    def set_tuning(self, tp: int = 0, block: int = 0, reach: int = 0):
-        _ck(lib().md_set_tuning(self._h, int(tp), int(block), int(reach)), "md_set_tuning")
+    def set_tuning(self, tp: int = 0, block: int = 0, reach: int = 0, build_lanes: int = 0):
+        _ck(lib().md_set_tuning(self._h, int(tp), int(block), int(reach), int(build_lanes)),
+            "md_set_tuning")
 
     def get_tuning(self):
-        a, b, c = C.c_int(), C.c_int(), C.c_int()
-        _ck(lib().md_get_tuning(self._h, C.byref(a), C.byref(b), C.byref(c)), "md_get_tuning")
-        return a.value, b.value, c.value
+        """(tp, block, reach, build_lanes)"""
+        a, b, c, d = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        _ck(lib().md_get_tuning(self._h, C.byref(a), C.byref(b), C.byref(c), C.byref(d)),
+            "md_get_tuning")
+        return a.value, b.value, c.value, d.value
+
+    def set_list_capacity(self, n_max: int):
+        _ck(lib().md_set_list_capacity(self._h, int(n_max)), "md_set_list_capacity")
+
+    def set_path(self, path):
+        """'auto' / 'grid' / 'replica' (or 0 / 1 / 2)."""
+        code = {"auto": 0, "grid": 1, "replica": 2}.get(path, path)
+        _ck(lib().md_set_path(self._h, int(code)), "md_set_path")
 
     def set_graph_block(self, steps: int):
         _ck(lib().md_set_graph_block(self._h, int(steps)), "md_set_graph_block")

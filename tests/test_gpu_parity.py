@@ -115,6 +115,24 @@ def test_neighbor_sets_bit_exact(n, reach):
         np.testing.assert_array_equal(got, ref[i])
 
 
+@pytest.mark.parametrize("reach", [1, 2])
+def test_list_order_and_forces_independent_of_build_lanes(reach):
+    """The list build compacts accepted candidates in candidate order, so the list (order
+    included) and therefore the forces are bitwise the same for any lanes-per-particle."""
+    st = ka(1500, seed=77)
+    ref = None
+    for lanes in (1, 4, 8, 32):
+        with make_sim(KA, [st], tuning=(2, 128, reach, lanes)) as sim:
+            f, u, w = sim.forces(0)
+            counts, nb = sim.neighbors(0)
+        if ref is None:
+            ref = (f, counts, nb)
+            continue
+        np.testing.assert_array_equal(counts, ref[1])
+        np.testing.assert_array_equal(nb, ref[2])
+        np.testing.assert_array_equal(f, ref[0])
+
+
 def test_neighbor_sets_fp64_mode_near_threshold_only():
     st = ka(1000, seed=13)
     with make_sim(KA, [st], precision="fp64") as sim:
@@ -308,6 +326,24 @@ def test_overflow_recovers_to_identical_forces():
         assert rel_rms(f, fr) <= 1e-5
 
 
+def test_overflow_during_stepping_is_redone_exactly():
+    """Grid path: steps after an overfull build are skipped on the device and redone after the
+    capacity grows, giving the same trajectory as a run that never overflowed."""
+    st = ka(1500, seed=61)
+    outs = []
+    for cap in (None, 30):
+        with make_sim(KA, [st], integrator="nvt", dt=0.0025, T=0.8, graph_block=10) as sim:
+            sim.set_path("grid")
+            if cap:
+                sim.set_list_capacity(cap)
+            sim.step(100)
+            outs.append(sim.get_state(0))
+            if cap:
+                assert sim.stats()["overflows"] >= 1
+    for u, v in zip(*outs):
+        np.testing.assert_array_equal(u, v)
+
+
 def test_runaway_displacement_is_reported():
     from paper_1506_05094_gb300 import MDError
 
@@ -324,11 +360,82 @@ def test_autotune_runs_and_caches(tmp_path):
     cache = tmp_path / "tune.txt"
     with make_sim(KA, [st], integrator="nvt", dt=0.0025, T=0.8) as sim:
         before = sim.get_state(0)
-        tp, block, reach = sim.autotune(str(cache), steps_per_trial=20)
+        tuned = sim.autotune(str(cache), steps_per_trial=20)
         after = sim.get_state(0)
         for x, y in zip(before, after):
             np.testing.assert_array_equal(x, y)      # the search leaves the state unchanged
         _check_forces(sim, st, KA)
     assert cache.exists() and cache.read_text().strip()
     with make_sim(KA, [st], integrator="nvt", dt=0.0025, T=0.8) as sim2:
-        assert sim2.autotune(str(cache), steps_per_trial=20) == (tp, block, reach)
+        assert sim2.autotune(str(cache), steps_per_trial=20) == tuned
+
+
+# ------------------------------------------------------------------ replica-resident kernel
+
+def _ensemble(sizes, seed0=100):
+    return [ka(n, T=0.8, seed=seed0 + k) for k, n in enumerate(sizes)]
+
+
+def _traj(sts, path, steps, tuning=(1, 128, 2, 8), graph_block=20):
+    with make_sim(KA, sts, integrator="nvt", dt=0.0025, T=0.8, tuning=tuning,
+                  graph_block=graph_block) as sim:
+        sim.set_path(path)
+        sim.step(steps)
+        out = [sim.get_state(r) for r in range(len(sts))]
+        en = [sim.energies(r) for r in range(len(sts))]
+        st = sim.stats()
+    return out, en, st
+
+
+@pytest.mark.parametrize("tuning", [(1, 128, 2, 8), (4, 256, 2, 32), (2, 64, 3, 8)])
+def test_replica_resident_path_bit_identical_to_grid(tuning):
+    """Same slot order, list order and reduction tree: the two kernel paths agree bit for bit
+    (NVT, 300 steps, with rebuilds inside the replica-resident kernel)."""
+    sts = _ensemble([512, 1000, 700, 2048, 777, 1500])
+    a, ea, sa = _traj(sts, "replica", 300, tuning)
+    b, eb, sb = _traj(sts, "grid", 300, tuning)
+    assert sa["path"] == 2 and sb["path"] == 1
+    assert sa["replica_rebuilds"] > len(sts)          # rebuilds happened in-kernel
+    for x, y in zip(a, b):
+        for u, v in zip(x, y):
+            np.testing.assert_array_equal(u, v)
+    for x, y in zip(ea, eb):
+        assert x["U"] == y["U"] and x["xi"] == y["xi"] and x["K_plus"] == y["K_plus"]
+
+
+def test_replica_resident_overflow_falls_back_exactly():
+    """An overfull list in the replica-resident kernel switches that replica to list-free forces
+    (and a rebuild every step) until the host grows the capacity, so no replica falls behind and
+    the trajectory stays the grid path's up to FP32 summation order (the grid path halts and redoes
+    the steps instead; the extra rebuilds reorder the neighbour sums)."""
+    sts = _ensemble([1200, 900, 1100], seed0=300)
+    res = []
+    for path in ("replica", "grid"):
+        with make_sim(KA, sts, integrator="nvt", dt=0.0025, T=0.8, tuning=(1, 128, 2, 8),
+                      graph_block=0) as sim:
+            sim.set_path(path)
+            sim.set_list_capacity(40)          # far below the ~90 neighbours at rho = 1.2
+            sim.step(30)
+            st = sim.stats()
+            assert st["overflows"] >= 1 and st["n_max"] > 40
+            assert all(sim.energies(r)["step"] == 29 for r in range(len(sts)))
+            res.append([sim.get_state(r) for r in range(len(sts))])
+    for x, y in zip(*res):
+        np.testing.assert_allclose(x[0], y[0], rtol=0, atol=1e-5)      # positions
+        np.testing.assert_array_equal(x[1], y[1])                    # images
+        np.testing.assert_allclose(x[2], y[2], rtol=0, atol=1e-4)      # velocities
+
+
+def test_replica_resident_matches_oracle_trajectory():
+    sts = _ensemble([600, 1000], seed0=400)
+    with make_sim(KA, sts, integrator="nvt", dt=0.0025, T=0.8, graph_block=10) as sim:
+        sim.set_path("replica")
+        sim.step(50)
+        for r, st in enumerate(sts):
+            ref = oracle.Run(st.pos, f32(st.vel), st.types, st.L, KA, "nvt", 0.0025, T=0.8)
+            log = ref.run(50)
+            e = sim.energies(r)
+            assert e["U"] == pytest.approx(log[-1, 0], rel=2e-5)
+            assert e["K_plus"] == pytest.approx(log[-1, 3], rel=2e-5)
+            x, _ = sim.unwrapped(r)
+            assert np.sqrt(np.mean((x - ref.pos) ** 2)) < 1e-4
