@@ -213,6 +213,34 @@ int md_load_checkpoint(md_sim *sim, const void *buf, size_t bytes);
 void md_destroy(md_sim *sim);
 const char *md_strerror(int status);
 
+/* Forces of one system for callers that cannot allocate device memory at call time.
+ *
+ * The paper has no counterpart: this entry point exists for callers that may not call
+ * cudaMalloc when they need forces -- for instance a caller in the middle of capturing a CUDA
+ * stream (allocation is not permitted there), a latency-critical loop that must never enter an
+ * allocator, or a host framework that owns all device memory.  It needs no md_sim and allocates
+ * nothing: inputs and outputs are the caller's device buffers, and the scratch it needs (the
+ * particles sorted by cell) lives in one fixed array that every GPU loading this library reserves
+ * (about 160 KB) and keeps until the process exits.
+ *
+ *   pos   (n,3) FP64 device array, any periodic image;  type (n) int32 device array;
+ *   L     cubic box edge, > 2 rc_max;  params n_types x n_types HOST array (symmetric);
+ *   f     (n,3) FP64 device output;  u, w (n) FP64 device outputs or NULL (u_i = 1/2 sum u_SP,
+ *         w_i = 1/6 sum r.F);  uw: 2 FP64 device outputs (U, W) or NULL;
+ *   cuda_stream: stream to run on (NULL = the legacy default stream).
+ * Limits: n <= MD_STATIC_MAX_PARTICLES and (floor(L / rc_max))^3 <= MD_STATIC_MAX_CELLS; larger
+ * inputs return MD_EINVAL with a message on stderr.  Arithmetic is the mixed-precision pair math
+ * of md_sim (forces agree with md_get_forces to FP32 summation order).
+ * The first call on a device looks up the scratch array's device address (once per device);
+ * make that first call before any stream capture.  All calls share the one scratch array, which
+ * keeps the last call's contents: calls that overlap on the GPU (other streams, other host
+ * threads) race on it and must be serialised by the caller.  Returns MD_OK once the work is
+ * queued on the stream. */
+enum { MD_STATIC_MAX_PARTICLES = 8192, MD_STATIC_MAX_CELLS = 4096 };
+int md_forces_static(const double *pos, const int *type, int n, double L, int n_types,
+                     const md_pair *params, double *f, double *u, double *w, double *uw,
+                     void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

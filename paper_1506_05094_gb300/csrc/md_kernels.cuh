@@ -504,12 +504,8 @@ __global__ void __launch_bounds__(1024) k_step(const StepArgs<R> a) {
     __syncthreads();
     if (s_skip) return;
 
-    // the block runs blockDim / tile_threads tiles of the grid kernel's shape side by side
-    const int TT = a.tile_threads;
-    const int P = TT / TP;
-    const int tpb_tiles = blockDim.x / TT;
-    const int tsub = threadIdx.x / TT;
-    const int lp = (threadIdx.x % TT) / TP, lt = threadIdx.x % TP;
+    const int P = blockDim.x / TP;
+    const int lp = threadIdx.x / TP, lt = threadIdx.x % TP;
     const int li = (tile - S.tile_off) * P + lp;
     const bool active = li < S.n;
     const int i = S.off + li;

@@ -28,7 +28,8 @@ SYMBOLS = ("md_create", "md_set_integrator", "md_set_state", "md_set_stream", "m
            "md_set_tuning", "md_get_tuning", "md_set_list_capacity", "md_set_path",
            "md_set_graph_block", "md_autotune",
            "md_get_stats", "md_profile", "md_set_log", "md_get_log", "md_checkpoint_size",
-           "md_save_checkpoint", "md_load_checkpoint", "md_destroy", "md_strerror")
+           "md_save_checkpoint", "md_load_checkpoint", "md_destroy", "md_strerror",
+           "md_forces_static")
 
 
 class md_pair(C.Structure):
@@ -104,6 +105,7 @@ def lib():
         "md_load_checkpoint": [p, p, C.c_size_t],
         "md_destroy": [p],
         "md_strerror": [i],
+        "md_forces_static": [p, p, i, d, i, C.POINTER(md_pair), p, p, p, p, p],
     }
     for name, args in sig.items():
         fn = getattr(L, name)

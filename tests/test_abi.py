@@ -73,3 +73,13 @@ def test_null_handles_are_rejected(L):
     assert L.md_sync(None) == md.MD_EINVAL
     assert L.md_set_graph_block(None, 10) == md.MD_EINVAL
     L.md_destroy(None)
+
+
+def test_static_entry_point_rejects_oversized_inputs_on_the_host(L):
+    """md_forces_static checks its fixed scratch limit before touching the device."""
+    pairs = (md.md_pair * 1)(md.md_pair(1.0, 1.0, 2.5))
+    dummy = C.c_void_p(16)   # never dereferenced: the size check fails first
+    code = L.md_forces_static(dummy, dummy, 8193, 30.0, 1, pairs, dummy, None, None, None, None)
+    assert code == md.MD_EINVAL
+    code = L.md_forces_static(dummy, dummy, 100, 4.0, 1, pairs, dummy, None, None, None, None)
+    assert code == md.MD_EINVAL   # box too small for the minimum image
