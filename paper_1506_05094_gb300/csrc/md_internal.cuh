@@ -151,6 +151,9 @@ template <typename R> struct RebuildArgs {
     int *plan_rep, *plan_pp, *plan_pc;
     int nsm;                 // SMs, for the persistent grids
     int tpb;                 // lanes per particle in the list build
+    int sort_small;          // 1: one-CTA-per-replica fused sort (k_sort_small)
+    int sort_nmax, sort_cmax;
+    size_t sort_smem;
     const SysDesc *sys;
     const PairTab *tab;
     int ntypes;
@@ -169,6 +172,10 @@ template <typename R> cudaError_t launch_rebuild(const RebuildArgs<R> &a, cudaSt
 template <typename R> cudaError_t launch_rebuild_timed(const RebuildArgs<R> &a, cudaStream_t s,
                                                        cudaEvent_t e0, cudaEvent_t e1);
 cudaError_t launch_arm(const Ctrl *ctrl, cudaGraphConditionalHandle h, cudaStream_t s);
+template <typename R> cudaError_t prepare_sort_small(size_t smem);
+inline size_t sort_small_smem_bytes(int nmax, int cmax) {
+    return (size_t)(2 * cmax + 1 + 3 * nmax) * 4;
+}
 // Replica-resident step kernel (FP32 / mixed precision only).
 cudaError_t launch_rep(const StepArgs<float> &a, const RebuildArgs<float> &b, int tp, int block,
                        int grid, size_t smem, cudaStream_t s);

@@ -787,10 +787,10 @@ template <typename R> __global__ void k_gather(const RebuildArgs<R> a) {
 // for every TPB.  Candidate indices are local (0..n-1 of the replica, or global slots when
 // base = 0 and the cell starts are global); the list stores slot = base + j.
 // Returns the full count (which may exceed nmax).
-template <typename R, int TPB, typename KeySrc, typename StartSrc>
+template <typename R, int TPB, bool STAGE, typename KeySrc, typename StartSrc>
 __device__ __forceinline__ int build_one(const SysDesc &S, const KeySrc &K, const StartSrc &CS,
                                          int self, int slot_i, int base, int *nbl, int nmax,
-                                         const R *s_thr, int ntypes) {
+                                         const R *s_thr, int ntypes, int2 *s_rng) {
     typedef typename V4T<R>::t V4;
     const int lt = threadIdx.x % TPB;
     const int lane = threadIdx.x & 31;
@@ -803,44 +803,53 @@ __device__ __forceinline__ int build_one(const SysDesc &S, const KeySrc &K, cons
     const int c = cell_index(ki, S);
     const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
     const bool full = (span == nc);
-    int cnt = 0;
-    for (int oz = 0; oz < span; ++oz) {
+    int xa0, xa1, xb0 = 0, xb1 = -1;   // x range of every row as one or two cell ranges
+    if (full) { xa0 = 0; xa1 = nc - 1; }
+    else {
+        const int x0 = cx - reach, x1 = cx + reach;
+        if (x0 < 0) { xa0 = x0 + nc; xa1 = nc - 1; xb0 = 0; xb1 = x1; }
+        else if (x1 >= nc) { xa0 = x0; xa1 = nc - 1; xb0 = 0; xb1 = x1 - nc; }
+        else { xa0 = x0; xa1 = x1; }
+    }
+    // range q of the stencil: row q/2 in (z, y) order, part q%2 of its x extent
+    auto range = [&](int q) -> int2 {
+        const int rowi = q >> 1, part = q & 1;
+        const int oz = rowi / span, oy = rowi % span;
         const int zz = full ? oz : (cz - reach + oz + nc) % nc;
-        for (int oy = 0; oy < span; ++oy) {
-            const int yy = full ? oy : (cy - reach + oy + nc) % nc;
-            const int row = (zz * nc + yy) * nc;
-            int xa0, xa1, xb0 = 0, xb1 = -1;   // x range of the row as one or two cell ranges
-            if (full) { xa0 = 0; xa1 = nc - 1; }
-            else {
-                const int x0 = cx - reach, x1 = cx + reach;
-                if (x0 < 0) { xa0 = x0 + nc; xa1 = nc - 1; xb0 = 0; xb1 = x1; }
-                else if (x1 >= nc) { xa0 = x0; xa1 = nc - 1; xb0 = 0; xb1 = x1 - nc; }
-                else { xa0 = x0; xa1 = x1; }
+        const int yy = full ? oy : (cy - reach + oy + nc) % nc;
+        const int row = (zz * nc + yy) * nc;
+        const int lo = part ? xb0 : xa0, hi = part ? xb1 : xa1;
+        return (hi < lo) ? make_int2(0, 0) : make_int2(CS(row + lo), CS(row + hi + 1));
+    };
+    const int nr = span * span * 2;
+    if (STAGE) {
+        // stage every range with independent loads spread over the lanes, so the cellStart
+        // latency is paid once instead of once per row
+        for (int q = lt; q < nr; q += TPB) s_rng[q] = range(q);
+        __syncwarp(gmask);
+    }
+    int cnt = 0;
+    for (int q = 0; q < nr; ++q) {
+        const int2 rg = STAGE ? s_rng[q] : range(q);
+        for (int b0 = rg.x; b0 < rg.y; b0 += TPB) {
+            const int j = b0 + lt;
+            bool ok = false;
+            if (j < rg.y && j != self) {
+                const V4 kj = K(j);
+                const R dx = min_image_exact(kj.x - ki.x, L, invL);
+                const R dy = min_image_exact(kj.y - ki.y, L, invL);
+                const R dz = min_image_exact(kj.z - ki.z, L, invL);
+                ok = dist2_exact(dx, dy, dz) < s_thr[ti * ntypes + type_of(kj)];
             }
-            for (int part = 0; part < 2; ++part) {
-                const int lo = part ? xb0 : xa0, hi = part ? xb1 : xa1;
-                if (hi < lo) continue;
-                const int js = CS(row + lo), je = CS(row + hi + 1);
-                for (int b0 = js; b0 < je; b0 += TPB) {
-                    const int j = b0 + lt;
-                    bool ok = false;
-                    if (j < je && j != self) {
-                        const V4 kj = K(j);
-                        const R dx = min_image_exact(kj.x - ki.x, L, invL);
-                        const R dy = min_image_exact(kj.y - ki.y, L, invL);
-                        const R dz = min_image_exact(kj.z - ki.z, L, invL);
-                        ok = dist2_exact(dx, dy, dz) < s_thr[ti * ntypes + type_of(kj)];
-                    }
-                    const unsigned m = __ballot_sync(gmask, ok);
-                    if (ok) {
-                        const int sl = cnt + __popc(m & below);
-                        if (sl < nmax) nbl[nbl_offset(slot_i, sl, nmax)] = base + j;
-                    }
-                    cnt += __popc(m);
-                }
+            const unsigned m = __ballot_sync(gmask, ok);
+            if (ok) {
+                const int sl = cnt + __popc(m & below);
+                if (sl < nmax) nbl[nbl_offset(slot_i, sl, nmax)] = base + j;
             }
+            cnt += __popc(m);
         }
     }
+    if (STAGE) __syncwarp(gmask);   // the staged ranges are reused by the group's next particle
     return cnt;
 }
 
@@ -854,10 +863,15 @@ struct GlobalStart {   // cell starts of replica S in the global cellStart array
     __device__ __forceinline__ int operator()(int c) const { return cs[cell_off + c]; }
 };
 
-template <typename R, int TPB> __global__ void k_build(const RebuildArgs<R> a) {
+// largest stencil: reach 3 -> 7 x 7 rows, two ranges each
+#define MD_MAX_RANGES 98
+#define MD_BUILD_BLOCK 128
+
+template <typename R, int TPB> __global__ void __launch_bounds__(MD_BUILD_BLOCK) k_build(const RebuildArgs<R> a) {
     typedef typename V4T<R>::t V4;
     if (rebuild_off(a.ctrl)) return;
     __shared__ R s_thr[MD_MAX_PAIRS];
+    __shared__ int2 s_rng_all[MD_BUILD_BLOCK / TPB][MD_MAX_RANGES];
     const int npair = a.ntypes * a.ntypes;
     for (int p = threadIdx.x; p < npair; p += blockDim.x)
         s_thr[p] = sizeof(R) == 4 ? (R)a.tab[p].thr2 : (R)a.tab[p].thr2d;
@@ -871,7 +885,8 @@ template <typename R, int TPB> __global__ void k_build(const RebuildArgs<R> a) {
         const SysDesc &S = a.sys[r];
         GlobalKey<R> K{Kp};
         GlobalStart CS{a.cell_start, S.cell_off};
-        int cnt = build_one<R, TPB>(S, K, CS, i, i, 0, a.nbl, a.nmax, s_thr, a.ntypes);
+        int cnt = build_one<R, TPB, true>(S, K, CS, i, i, 0, a.nbl, a.nmax, s_thr, a.ntypes,
+                                          s_rng_all[threadIdx.x / TPB]);
         if (threadIdx.x % TPB == 0) {
             if (cnt > a.nmax) {   // Sec. 4: out of space -> flag for the host, which doubles n_max
                 atomicMax(&a.ctrl->max_count, cnt);
@@ -1105,8 +1120,8 @@ __global__ void __launch_bounds__(1024) k_rep(const StepArgs<R> a, const Rebuild
             SharedKey<R> K{s_pos};
             SharedStart CS{s_cs};
             for (int g = threadIdx.x / TPB; g < n; g += blockDim.x / TPB) {
-                int cnt = build_one<R, TPB>(S, K, CS, g, off + g, off, b.nbl, b.nmax, s_thr,
-                                            a.ntypes);
+                int cnt = build_one<R, TPB, false>(S, K, CS, g, off + g, off, b.nbl, b.nmax,
+                                                   s_thr, a.ntypes, nullptr);
                 if (threadIdx.x % TPB == 0) {
                     if (cnt > b.nmax) {
                         atomicMax(&a.ctrl->max_count, cnt);
@@ -1177,6 +1192,68 @@ __global__ void __launch_bounds__(1024) k_rep(const StepArgs<R> a, const Rebuild
     }
     __syncthreads();
     if (s_glast) close_step(a);
+}
+
+
+// ------------------------------------------------------------------------------------------------
+// Fused sort for replicas that fit in shared memory (grid path): one CTA per rebuilt replica
+// performs bin, exclusive scan (cellStart), slot scatter, in-cell order by user id and the gather
+// into the scratch arrays -- the work of k_bin .. k_gather in one launch.  k_build follows.
+// ------------------------------------------------------------------------------------------------
+template <typename R> __global__ void __launch_bounds__(512) k_sort_small(const RebuildArgs<R> a) {
+    extern __shared__ __align__(16) int sm[];
+    __shared__ int s_warp[32];
+    if (rebuild_off(a.ctrl)) return;
+    int *s_cnt = sm;                          // sort_cmax
+    int *s_cs = s_cnt + a.sort_cmax;          // sort_cmax + 1
+    int *s_cell = s_cs + a.sort_cmax + 1;     // sort_nmax
+    int *s_perm = s_cell + a.sort_nmax;       // sort_nmax
+    int *s_id = s_perm + a.sort_nmax;         // sort_nmax
+    const int nf = a.plan->nflag;
+    for (int b = blockIdx.x; b < nf; b += gridDim.x) {
+        const int r = a.plan_rep[b];
+        const SysDesc S = a.sys[r];
+        const int n = S.n, off = S.off, C = S.nc * S.nc * S.nc;
+        for (int c = threadIdx.x; c < C; c += blockDim.x) s_cnt[c] = 0;
+        __syncthreads();
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            const int c = cell_index(a.key[off + k], S);
+            s_cell[k] = c;
+            s_id[k] = a.id[off + k];
+            atomicAdd(s_cnt + c, 1);
+        }
+        __syncthreads();
+        block_scan_cells(s_cnt, s_cs, C, s_warp);
+        for (int c = threadIdx.x; c < C; c += blockDim.x) s_cnt[c] = s_cs[c];
+        __syncthreads();
+        for (int k = threadIdx.x; k < n; k += blockDim.x)
+            s_perm[atomicAdd(s_cnt + s_cell[k], 1)] = k;
+        __syncthreads();
+        for (int c = threadIdx.x; c < C; c += blockDim.x) {   // deterministic: by user id
+            const int s0 = s_cs[c], e0 = s_cs[c + 1];
+            for (int q = s0 + 1; q < e0; ++q) {
+                const int v = s_perm[q], key = s_id[v];
+                int m = q - 1;
+                while (m >= s0 && s_id[s_perm[m]] > key) { s_perm[m + 1] = s_perm[m]; --m; }
+                s_perm[m + 1] = v;
+            }
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < n; q += blockDim.x) {
+            const int o = off + s_perm[q], d = off + q;
+            a.tpos[d] = a.pos[o];
+            if (!a.key_is_pos) a.tkey[d] = a.key[o];
+            a.txd[d] = a.xd[o];
+            a.tyd[d] = a.yd[o];
+            a.tzd[d] = a.zd[o];
+            a.tvel[d] = a.vel[o];
+            a.timg[d] = a.img[o];
+            a.tid[d] = s_id[s_perm[q]];
+        }
+        for (int c = threadIdx.x; c < C; c += blockDim.x) a.cell_start[S.cell_off + c] = off + s_cs[c];
+        if (threadIdx.x == 0) a.th[r].rebuilds += 1;
+        __syncthreads();
+    }
 }
 
 }  // namespace md

@@ -65,6 +65,8 @@ struct md_sim {
     bool rep_ok = false;     // replica-resident kernel usable with the current shape
     size_t rep_smem = 0;
     int rep_threads = 512, rep_ctas = 1;
+    bool sort_small = false;
+    size_t sort_smem = 0;
     int rep_nmax = 0, rep_cmax = 0;
     int *rep_order = nullptr;
     int nsm = 148;
@@ -211,6 +213,17 @@ int configure_layout(md_sim *s, bool realloc_cells) {
         s->rep_nmax = std::max(s->rep_nmax, s->sys[r].n);
         s->rep_cmax = std::max(s->rep_cmax, s->sys[r].nc * s->sys[r].nc * s->sys[r].nc);
     }
+    // fused one-CTA-per-replica sort when the largest replica fits in shared memory
+    {
+        int optin2 = 0;
+        cudaDeviceGetAttribute(&optin2, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
+        s->sort_smem = sort_small_smem_bytes(s->rep_nmax, s->rep_cmax);
+        s->sort_small = s->rep_nmax <= 16384 && s->sort_smem + 1024 <= (size_t)optin2 &&
+                        (s->precision == MD_FP64 ? prepare_sort_small<double>(s->sort_smem)
+                                                 : prepare_sort_small<float>(s->sort_smem)) ==
+                            cudaSuccess;
+        cudaGetLastError();
+    }
     s->rep_threads = std::max(s->block, 512);
     s->rep_smem = rep_smem_bytes(s->rep_nmax, s->rep_cmax, s->block, s->tp, s->rep_threads);
     int optin = 0, per_sm = 0;
@@ -340,6 +353,10 @@ template <typename R> RebuildArgs<R> rebuild_args(md_sim *s, int parity, const v
     a.plan_pc = s->b.plan_arr + 2 * s->R + 1;
     a.nsm = s->nsm;
     a.tpb = s->tpb;
+    a.sort_small = s->sort_small ? 1 : 0;
+    a.sort_nmax = s->rep_nmax;
+    a.sort_cmax = s->rep_cmax;
+    a.sort_smem = s->sort_smem;
     a.sys = s->b.sys;
     a.tab = s->b.tab;
     a.ntypes = s->nt;
