@@ -142,8 +142,9 @@ def make_sim(wl, stream, precision="mixed"):
 
 
 def kernel_source_hash():
+    """Hash of the sources the fused step kernel is compiled from."""
     h = hashlib.sha256()
-    for f in ("md_kernels.cuh", "md_launch.inc", "md_internal.cuh"):
+    for f in ("md_common.cuh", "md_step.cuh", "md_internal.cuh"):
         with open(os.path.join(ROOT, "paper_1506_05094_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -312,7 +313,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip single-system/e2e/cpu legs")
     ap.add_argument("--replicas", type=int, default=None, help="trim the ensemble (profiling)")
     ap.add_argument("--tuning", default=None, help="tp,block,reach[,lanes]: skip the autotuner")
-    ap.add_argument("--path", default=None, choices=["grid", "replica"],
+    ap.add_argument("--path", default=None, choices=["grid", "replica", "staged"],
                     help="force a kernel path (default: the autotuner's choice)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -350,7 +351,7 @@ def main():
         tuning = sim.autotune(os.path.join(ROOT, "paper_1506_05094_gb300", "tune_cache.txt"), 50)
     if args.path:
         sim.set_path(args.path)
-    path = "replica" if sim.stats()["path"] == 2 else "grid"
+    path = {1: "grid", 2: "replica", 3: "staged"}[sim.stats()["path"]]
     gb = pick_block(args.steps)
     sim.set_graph_block(gb)
     sim.step(gb)                     # capture the graph (setup, untimed)
@@ -378,10 +379,11 @@ def main():
     # an odd K ends with one plain step (its 6 rebuild kernels launch and exit if not needed)
     n_graphs = args.steps // gb
     rem = args.steps - n_graphs * gb
+    nk = st1["rebuild_kernels"]
     if path == "replica":   # one replica-resident launch per step, rebuilds inside it
         gpu_launches = args.steps
-    else:                   # + arm kernel per graph, 7-kernel rebuild pass per IF body executed
-        gpu_launches = args.steps + n_graphs + 7 * passes + 7 * rem
+    else:                   # + arm kernel per graph, nk-kernel rebuild pass per IF body executed
+        gpu_launches = args.steps + n_graphs + nk * passes + nk * rem
 
     # dominant kernel: fused step kernel, plain launches with CUDA events on the sim's stream
     prof = sim.profile(50)

@@ -90,7 +90,8 @@ typedef struct {
     int max_neighbors;          /* largest neighbour count at the most recent build */
     int tp, block, reach;       /* threads per particle, threads per block, cell stencil reach */
     int build_lanes;            /* lanes per particle in the list build */
-    int path;                   /* 1 grid kernels, 2 replica-resident kernel */
+    int path;                   /* 1 grid, 2 replica-resident, 3 grid with staged positions */
+    int rebuild_kernels;        /* kernels launched per rebuild pass on the grid path */
     int graph_block;            /* steps per captured CUDA graph (0 = plain launches) */
     long long n_total;          /* particles over all replicas */
     long long neighbor_entries; /* sum of neighbour counts at the most recent build */
@@ -171,10 +172,12 @@ int md_set_list_capacity(md_sim *sim, int n_max);
 
 /* Kernel path: 1 = grid kernels (one CTA per tile of any replica; the rebuild is a chain of
  * kernels behind a CUDA-graph IF node), 2 = replica-resident kernel (persistent CTAs that each
- * run a whole step of one replica at a time in shared memory, rebuild included; mixed precision,
- * replicas up to the shared-memory limit), 0 = automatic (2 when it applies and there are at least
- * 32 replicas).  Both paths give the same results bit for bit.  MD_EINVAL if 2 does not apply. */
-enum { MD_PATH_AUTO = 0, MD_PATH_GRID = 1, MD_PATH_REPLICA = 2 };
+ * run a whole step of one replica at a time in shared memory, rebuild included), 3 = grid kernels
+ * with each tile's replica positions staged in shared memory for the neighbour gathers.  2 and 3
+ * are mixed precision only and need replicas that fit in shared memory.  0 = automatic (2 when it
+ * applies and there are at least 32 replicas, else 1).  All paths give the same results bit for
+ * bit.  MD_EINVAL if the requested path does not apply. */
+enum { MD_PATH_AUTO = 0, MD_PATH_GRID = 1, MD_PATH_REPLICA = 2, MD_PATH_STAGED = 3 };
 int md_set_path(md_sim *sim, int path);
 
 /* Steps captured per CUDA graph replay (even, >= 2), or 0 for plain kernel launches with

@@ -180,6 +180,10 @@ inline size_t sort_small_smem_bytes(int nmax, int cmax) {
 cudaError_t launch_rep(const StepArgs<float> &a, const RebuildArgs<float> &b, int tp, int block,
                        int grid, size_t smem, cudaStream_t s);
 cudaError_t prepare_rep(int tp, int tpb, bool single, size_t smem);
+// Grid step kernel with the replica's positions staged in shared memory (FP32 only).
+cudaError_t launch_step_staged(const StepArgs<float> &a, int tp, int block, int ntiles,
+                               size_t smem, cudaStream_t s);
+cudaError_t prepare_step_staged(int tp, bool single, size_t smem);
 // Dynamic shared memory of the replica-resident kernel for replicas of up to nmax particles and
 // cmax cells with `block` threads and tp threads per particle.
 inline size_t rep_smem_bytes(int nmax, int cmax, int block, int tp, int cta_threads) {

@@ -51,3 +51,33 @@ cudaError_t launch_rep(const StepArgs<float> &a, const RebuildArgs<float> &b, in
     void *args[] = {(void *)&a, (void *)&b};
     return cudaLaunchKernel(f, dim3(grid), dim3(block), args, smem, s);
 }
+
+// ---- grid step kernel with staged replica positions
+namespace {
+template <bool SINGLE> void *staged_fn(int tp) {
+    switch (tp) {
+    case 1: return (void *)md::k_step<float, 1, SINGLE, true>;
+    case 2: return (void *)md::k_step<float, 2, SINGLE, true>;
+    case 4: return (void *)md::k_step<float, 4, SINGLE, true>;
+    case 8: return (void *)md::k_step<float, 8, SINGLE, true>;
+    case 16: return (void *)md::k_step<float, 16, SINGLE, true>;
+    case 32: return (void *)md::k_step<float, 32, SINGLE, true>;
+    default: return nullptr;
+    }
+}
+}  // namespace
+
+cudaError_t prepare_step_staged(int tp, bool single, size_t smem) {
+    void *f = single ? staged_fn<true>(tp) : staged_fn<false>(tp);
+    if (!f) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t launch_step_staged(const StepArgs<float> &a, int tp, int block, int ntiles,
+                               size_t smem, cudaStream_t s) {
+    void *f = a.ntypes == 1 ? staged_fn<true>(tp) : staged_fn<false>(tp);
+    if (!f) return cudaErrorInvalidValue;
+    if (ntiles <= 0) return cudaSuccess;
+    void *args[] = {(void *)&a};
+    return cudaLaunchKernel(f, dim3(ntiles), dim3(block), args, smem, s);
+}

@@ -1,0 +1,356 @@
+// md_rebuild.cuh -- the cell-sorted rebuild of the neighbour list (Sec. 7, Fig. 4) on the grid
+// path: work plan, bin / scan / scatter / in-cell order / gather (or the fused one-CTA sort), build.
+#pragma once
+#include "md_step.cuh"
+
+namespace md {
+
+// ------------------------------------------------------------------------------------------------
+// Rebuild (Sec. 7).  k_plan compacts the replicas whose need flag is set into a work list; the
+// other kernels grid-stride over that list only (no blocks are spent on replicas that keep their
+// list).  halt and need_any only change between passes, so every thread sees the same values.
+// An overflow does not stop a pass: the copy back of the permuted data must always complete.
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ bool rebuild_off(const Ctrl *c) {
+    return *(volatile const int *)&c->halt || !*(volatile const int *)&c->need_any;
+}
+
+// largest k in [0, n) with pfx[k] <= t  (pfx ascending, pfx[0] = 0)
+__device__ __forceinline__ int find_seg(const int *pfx, int n, int t) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pfx[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename V4> __device__ __forceinline__ int cell_index(const V4 &p, const SysDesc &S) {
+    const float cs = S.cell_scale;
+    int cx = __float2int_rd(__fmul_rn((float)p.x, cs));
+    int cy = __float2int_rd(__fmul_rn((float)p.y, cs));
+    int cz = __float2int_rd(__fmul_rn((float)p.z, cs));
+    cx = min(max(cx, 0), S.nc - 1);
+    cy = min(max(cy, 0), S.nc - 1);
+    cz = min(max(cz, 0), S.nc - 1);
+    return (cz * S.nc + cy) * S.nc + cx;
+}
+
+// One CTA: exclusive scans over replicas of (flagged, particles, cells) -> the pass's work list.
+template <typename R> __global__ void k_plan(const RebuildArgs<R> a) {
+    __shared__ int s_w[3][32];
+    const int R_ = a.nrep, nt = blockDim.x;
+    if (rebuild_off(a.ctrl)) {
+        if (threadIdx.x == 0) { a.plan->nflag = 0; a.plan->tot_p = 0; a.plan->tot_c = 0; }
+        return;
+    }
+    const int chunk = (R_ + nt - 1) / nt;
+    const int r0 = min(R_, (int)threadIdx.x * chunk), r1 = min(R_, r0 + chunk);
+    int f = 0, np = 0, nc = 0;
+    for (int r = r0; r < r1; ++r)
+        if (a.need_in[r]) {
+            const SysDesc &S = a.sys[r];
+            ++f; np += S.n; nc += S.nc * S.nc * S.nc;
+        }
+    int v[3] = {f, np, nc}, x[3];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        x[q] = v[q];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL_MASK, x[q], o);
+            if (lane >= o) x[q] += y;
+        }
+        if (lane == 31) s_w[q][warp] = x[q];
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            int t = (lane < (nt >> 5)) ? s_w[q][lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(FULL_MASK, t, o);
+                if (lane >= o) t += y;
+            }
+            s_w[q][lane] = t;
+        }
+    }
+    __syncthreads();
+    int of = x[0] - v[0] + (warp ? s_w[0][warp - 1] : 0);
+    int op = x[1] - v[1] + (warp ? s_w[1][warp - 1] : 0);
+    int oc = x[2] - v[2] + (warp ? s_w[2][warp - 1] : 0);
+    for (int r = r0; r < r1; ++r)
+        if (a.need_in[r]) {
+            const SysDesc &S = a.sys[r];
+            a.plan_rep[of] = r;
+            a.plan_pp[of] = op;
+            a.plan_pc[of] = oc;
+            ++of; op += S.n; oc += S.nc * S.nc * S.nc;
+        }
+    if (threadIdx.x == nt - 1) {
+        a.plan->nflag = of;
+        a.plan->tot_p = op;
+        a.plan->tot_c = oc;
+        a.plan_pp[of] = op;
+        a.plan_pc[of] = oc;
+        if (of > 0) a.ctrl->rebuild_passes += 1;
+    }
+}
+
+// particle t of the pass's work list -> (replica, slot)
+__device__ __forceinline__ void pass_particle(const int *pp, const int *rep, int nflag, int t,
+                                              const SysDesc *sys, int &r, int &i) {
+    const int k = find_seg(pp, nflag, t);
+    r = rep[k];
+    i = sys[r].off + (t - pp[k]);
+}
+
+template <typename R> __global__ void k_bin(const RebuildArgs<R> a) {
+    if (rebuild_off(a.ctrl)) return;
+    const int tot = a.plan->tot_p, nf = a.plan->nflag;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
+        int r, i;
+        pass_particle(a.plan_pp, a.plan_rep, nf, t, a.sys, r, i);
+        const SysDesc &S = a.sys[r];
+        const int c = S.cell_off + cell_index(a.key[i], S);
+        a.cell_of[i] = c;
+        a.rank[i] = atomicAdd(a.count + c, 1);
+    }
+}
+
+// Per replica: exclusive scan of the cell counts -> cellStart (Sec. 7); counts re-zeroed.
+template <typename R> __global__ void k_scan(const RebuildArgs<R> a) {
+    if (rebuild_off(a.ctrl)) return;
+    __shared__ int s_warp[32];
+    const int nf = a.plan->nflag;
+    for (int b = blockIdx.x; b < nf; b += gridDim.x) {
+        const int r = a.plan_rep[b];
+        const SysDesc &S = a.sys[r];
+        const int C = S.nc * S.nc * S.nc;
+        const int nt = blockDim.x;
+        const int chunk = (C + nt - 1) / nt;
+        const int c0 = min(C, (int)threadIdx.x * chunk), c1 = min(C, c0 + chunk);
+        int sum = 0;
+        for (int c = c0; c < c1; ++c) sum += a.count[S.cell_off + c];
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        int x = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL_MASK, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int v = (lane < (nt >> 5)) ? s_warp[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(FULL_MASK, v, o);
+                if (lane >= o) v += y;
+            }
+            s_warp[lane] = v;
+        }
+        __syncthreads();
+        int run = S.off + (x - sum) + (warp > 0 ? s_warp[warp - 1] : 0);
+        for (int c = c0; c < c1; ++c) {
+            const int n = a.count[S.cell_off + c];
+            a.cell_start[S.cell_off + c] = run;
+            a.count[S.cell_off + c] = 0;
+            run += n;
+        }
+        if (threadIdx.x == 0) a.th[r].rebuilds += 1;
+        __syncthreads();
+    }
+}
+
+template <typename R> __global__ void k_scatter(const RebuildArgs<R> a) {
+    if (rebuild_off(a.ctrl)) return;
+    const int tot = a.plan->tot_p, nf = a.plan->nflag;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
+        int r, i;
+        pass_particle(a.plan_pp, a.plan_rep, nf, t, a.sys, r, i);
+        a.perm[a.cell_start[a.cell_of[i]] + a.rank[i]] = i;
+    }
+}
+
+// Atomic slot order inside a cell is arbitrary (as with atomicInc in Sec. 6); restore a
+// deterministic order: by user id.
+template <typename R> __global__ void k_cellsort(const RebuildArgs<R> a) {
+    if (rebuild_off(a.ctrl)) return;
+    const int tot = a.plan->tot_c, nf = a.plan->nflag;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
+        const int k = find_seg(a.plan_pc, nf, t);
+        const int c = a.sys[a.plan_rep[k]].cell_off + (t - a.plan_pc[k]);
+        const int s = a.cell_start[c], e = a.cell_start[c + 1];
+        for (int q = s + 1; q < e; ++q) {
+            const int v = a.perm[q];
+            const int key = a.id[v];
+            int m = q - 1;
+            while (m >= s && a.id[a.perm[m]] > key) {
+                a.perm[m + 1] = a.perm[m];
+                --m;
+            }
+            a.perm[m + 1] = v;
+        }
+    }
+}
+
+template <typename R> __global__ void k_gather(const RebuildArgs<R> a) {
+    if (rebuild_off(a.ctrl)) return;
+    const int tot = a.plan->tot_p, nf = a.plan->nflag;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
+        int r, s;
+        pass_particle(a.plan_pp, a.plan_rep, nf, t, a.sys, r, s);
+        const int o = a.perm[s];
+        a.tpos[s] = a.pos[o];
+        if (!a.key_is_pos) a.tkey[s] = a.key[o];
+        a.txd[s] = a.xd[o];
+        a.tyd[s] = a.yd[o];
+        a.tzd[s] = a.zd[o];
+        a.tvel[s] = a.vel[o];
+        a.timg[s] = a.img[o];
+        a.tid[s] = a.id[o];
+    }
+}
+
+// List build from sorted cells (Fig. 4) for one particle.  TPB lanes per particle walk the
+// stencil as rows of cells along x: the cells (cx-reach .. cx+reach) of one (cy, cz) row hold one
+// contiguous range of sorted slots (two when the row wraps), so a row costs two cellStart reads
+// and its candidates are tested TPB at a time.  Accepted slots are compacted by ballot within the
+// lane group, in candidate order, so the list order -- and hence every force bit -- is the same
+// for every TPB.  Candidate indices are local (0..n-1 of the replica, or global slots when
+// base = 0 and the cell starts are global); the list stores slot = base + j.
+// Returns the full count (which may exceed nmax).
+template <typename R, int TPB, bool STAGE, typename KeySrc, typename StartSrc>
+__device__ __forceinline__ int build_one(const SysDesc &S, const KeySrc &K, const StartSrc &CS,
+                                         int self, int slot_i, int base, int *nbl, int nmax,
+                                         const R *s_thr, int ntypes, int2 *s_rng) {
+    typedef typename V4T<R>::t V4;
+    const int lt = threadIdx.x % TPB;
+    const int lane = threadIdx.x & 31;
+    const unsigned gmask = (TPB == 32) ? FULL_MASK : (((1u << TPB) - 1u) << (lane & ~(TPB - 1)));
+    const unsigned below = (1u << lane) - 1u;
+    const V4 ki = K(self);
+    const int ti = type_of(ki);
+    const R L = box_L<R>(S), invL = box_invL<R>(S);
+    const int nc = S.nc, span = S.span, reach = S.reach;
+    const int c = cell_index(ki, S);
+    const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
+    const bool full = (span == nc);
+    int xa0, xa1, xb0 = 0, xb1 = -1;   // x range of every row as one or two cell ranges
+    if (full) { xa0 = 0; xa1 = nc - 1; }
+    else {
+        const int x0 = cx - reach, x1 = cx + reach;
+        if (x0 < 0) { xa0 = x0 + nc; xa1 = nc - 1; xb0 = 0; xb1 = x1; }
+        else if (x1 >= nc) { xa0 = x0; xa1 = nc - 1; xb0 = 0; xb1 = x1 - nc; }
+        else { xa0 = x0; xa1 = x1; }
+    }
+    // range q of the stencil: row q/2 in (z, y) order, part q%2 of its x extent
+    auto range = [&](int q) -> int2 {
+        const int rowi = q >> 1, part = q & 1;
+        const int oz = rowi / span, oy = rowi % span;
+        const int zz = full ? oz : (cz - reach + oz + nc) % nc;
+        const int yy = full ? oy : (cy - reach + oy + nc) % nc;
+        const int row = (zz * nc + yy) * nc;
+        const int lo = part ? xb0 : xa0, hi = part ? xb1 : xa1;
+        return (hi < lo) ? make_int2(0, 0) : make_int2(CS(row + lo), CS(row + hi + 1));
+    };
+    const int nr = span * span * 2;
+    if (STAGE) {
+        // stage every range with independent loads spread over the lanes, so the cellStart
+        // latency is paid once instead of once per row
+        for (int q = lt; q < nr; q += TPB) s_rng[q] = range(q);
+        __syncwarp(gmask);
+    }
+    // each lane tests U candidates per pass, then U ballots in candidate order keep the
+    // compaction order of a one-candidate-per-lane walk (U = 1: rows hold ~20 candidates, wider
+    // passes leave lanes idle and measured slower)
+    constexpr int U = 1;
+    int cnt = 0;
+    for (int q = 0; q < nr; ++q) {
+        const int2 rg = STAGE ? s_rng[q] : range(q);
+        for (int b0 = rg.x; b0 < rg.y; b0 += TPB * U) {
+            bool ok[U];
+#pragma unroll
+            for (int uu = 0; uu < U; ++uu) {
+                const int j = b0 + uu * TPB + lt;
+                ok[uu] = false;
+                if (j < rg.y && j != self) {
+                    const V4 kj = K(j);
+                    const R dx = min_image_exact(kj.x - ki.x, L, invL);
+                    const R dy = min_image_exact(kj.y - ki.y, L, invL);
+                    const R dz = min_image_exact(kj.z - ki.z, L, invL);
+                    ok[uu] = dist2_exact(dx, dy, dz) < s_thr[ti * ntypes + type_of(kj)];
+                }
+            }
+#pragma unroll
+            for (int uu = 0; uu < U; ++uu) {
+                const unsigned m = __ballot_sync(gmask, ok[uu]);
+                if (ok[uu]) {
+                    const int sl = cnt + __popc(m & below);
+                    if (sl < nmax) nbl[nbl_offset(slot_i, sl, nmax)] = base + b0 + uu * TPB + lt;
+                }
+                cnt += __popc(m);
+            }
+        }
+    }
+    if (STAGE) __syncwarp(gmask);   // the staged ranges are reused by the group's next particle
+    return cnt;
+}
+
+template <typename R> struct GlobalKey {
+    const typename V4T<R>::t *p;
+    __device__ __forceinline__ typename V4T<R>::t operator()(int j) const { return p[j]; }
+};
+struct GlobalStart {   // cell starts of replica S in the global cellStart array
+    const int *cs;
+    int cell_off;
+    __device__ __forceinline__ int operator()(int c) const { return cs[cell_off + c]; }
+};
+
+// largest stencil: reach 3 -> 7 x 7 rows, two ranges each
+#define MD_MAX_RANGES 98
+#define MD_BUILD_BLOCK 128
+
+template <typename R, int TPB> __global__ void __launch_bounds__(MD_BUILD_BLOCK) k_build(const RebuildArgs<R> a) {
+    typedef typename V4T<R>::t V4;
+    if (rebuild_off(a.ctrl)) return;
+    __shared__ R s_thr[MD_MAX_PAIRS];
+    __shared__ int2 s_rng_all[MD_BUILD_BLOCK / TPB][MD_MAX_RANGES];
+    const int npair = a.ntypes * a.ntypes;
+    for (int p = threadIdx.x; p < npair; p += blockDim.x)
+        s_thr[p] = sizeof(R) == 4 ? (R)a.tab[p].thr2 : (R)a.tab[p].thr2d;
+    __syncthreads();
+    const int tot = a.plan->tot_p, nf = a.plan->nflag;
+    const int groups = gridDim.x * (blockDim.x / TPB);
+    const V4 *Kp = a.key_is_pos ? a.tpos : a.tkey;
+    for (int g = blockIdx.x * (blockDim.x / TPB) + threadIdx.x / TPB; g < tot; g += groups) {
+        int r, i;
+        pass_particle(a.plan_pp, a.plan_rep, nf, g, a.sys, r, i);
+        const SysDesc &S = a.sys[r];
+        GlobalKey<R> K{Kp};
+        GlobalStart CS{a.cell_start, S.cell_off};
+        int cnt = build_one<R, TPB, true>(S, K, CS, i, i, 0, a.nbl, a.nmax, s_thr, a.ntypes,
+                                          s_rng_all[threadIdx.x / TPB]);
+        if (threadIdx.x % TPB == 0) {
+            if (cnt > a.nmax) {   // Sec. 4: out of space -> flag for the host, which doubles n_max
+                atomicMax(&a.ctrl->max_count, cnt);
+                atomicExch(&a.ctrl->overflow, 1);
+                cnt = a.nmax;
+            }
+            a.nnb[i] = cnt;
+            a.pos[i] = a.tpos[i];
+            a.pos_build[i] = Kp[i];
+            a.xd[i] = a.txd[i];
+            a.yd[i] = a.tyd[i];
+            a.zd[i] = a.tzd[i];
+            a.vel[i] = a.tvel[i];
+            a.img[i] = a.timg[i];
+            a.id[i] = a.tid[i];
+        }
+    }
+}
+
+}  // namespace md

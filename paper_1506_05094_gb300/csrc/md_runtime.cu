@@ -67,6 +67,8 @@ struct md_sim {
     int rep_threads = 512, rep_ctas = 1;
     bool sort_small = false;
     size_t sort_smem = 0;
+    bool staged_ok = false;   // path 3: grid step kernel with replica positions in shared memory
+    size_t staged_smem = 0;
     int rep_nmax = 0, rep_cmax = 0;
     int *rep_order = nullptr;
     int nsm = 148;
@@ -224,6 +226,15 @@ int configure_layout(md_sim *s, bool realloc_cells) {
                             cudaSuccess;
         cudaGetLastError();
     }
+    {
+        int optin3 = 0;
+        cudaDeviceGetAttribute(&optin3, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
+        s->staged_smem = (size_t)s->rep_nmax * 16;
+        s->staged_ok = s->precision == MD_MIXED && s->staged_smem + 8192 <= (size_t)optin3 &&
+                       s->staged_smem <= 100 * 1024 &&
+                       prepare_step_staged(s->tp, s->nt == 1, s->staged_smem) == cudaSuccess;
+        cudaGetLastError();
+    }
     s->rep_threads = std::max(s->block, 512);
     s->rep_smem = rep_smem_bytes(s->rep_nmax, s->rep_cmax, s->block, s->tp, s->rep_threads);
     int optin = 0, per_sm = 0;
@@ -377,7 +388,7 @@ cudaError_t do_rebuild(md_sim *s, int parity, cudaStream_t st, const void *key =
 bool use_rep(const md_sim *s) {
     if (!s->rep_ok) return false;
     if (s->path == 2) return true;
-    if (s->path == 1) return false;
+    if (s->path == 1 || s->path == 3) return false;
     return s->R >= 32;   // auto: enough replicas to occupy every SM with whole replicas
 }
 
@@ -399,6 +410,8 @@ cudaError_t do_step(md_sim *s, int parity, cudaStream_t st, int force_only,
     StepArgs<float> a = step_args<float>(s, parity, force_only);
     a.next_handle = next;
     a.has_next = has_next;
+    if (s->path == 3 && s->staged_ok)
+        return launch_step_staged(a, s->tp, s->block, s->ntiles, s->staged_smem, st);
     return launch_step<float>(a, s->tp, s->block, s->ntiles, st);
 }
 
@@ -1145,9 +1158,10 @@ int md_set_list_capacity(md_sim *s, int n_max) {
 }
 
 int md_set_path(md_sim *s, int path) {
-    if (!s || path < 0 || path > 2) return MD_EINVAL;
+    if (!s || path < 0 || path > 3) return MD_EINVAL;
     if (s->sticky) return s->sticky;
     if (path == 2 && !s->rep_ok) return MD_EINVAL;
+    if (path == 3 && !s->staged_ok) return MD_EINVAL;
     if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(s, MD_ECUDA);
     destroy_graphs(s);
     s->path = path;
@@ -1189,7 +1203,8 @@ int md_get_stats(md_sim *s, md_stats *out) {
     out->block = s->block;
     out->reach = s->reach;
     out->build_lanes = s->tpb;
-    out->path = use_rep(s) ? 2 : 1;
+    out->path = use_rep(s) ? 2 : ((s->path == 3 && s->staged_ok) ? 3 : 1);
+    out->rebuild_kernels = s->sort_small ? 3 : 7;   // plan, [fused sort | 5 kernels], build
     out->graph_block = s->graph_block;
     out->n_total = s->ntot;
     out->neighbor_entries = ent;

@@ -1,0 +1,374 @@
+// md_step.cuh -- the grid step kernel (k_step) and the per-particle pieces it shares with the
+// replica-resident kernel: force sum over the list, integrator, tile and replica reductions.
+#pragma once
+#include "md_common.cuh"
+
+namespace md {
+
+// ------------------------------------------------------------------------------------------------
+// Per-particle pieces shared by the grid kernel (k_step) and the replica-resident kernel (k_rep).
+// ------------------------------------------------------------------------------------------------
+
+// Neighbour positions read from global memory through the read-only path (grid kernel) ...
+template <typename R> struct GlobalPos {
+    const typename V4T<R>::t *p;
+    __device__ __forceinline__ typename V4T<R>::t operator()(int j) const { return ld_nc(p + j); }
+};
+// ... or from the replica's positions staged in shared memory (slot j - off).
+template <typename R> struct SharedPos {
+    const typename V4T<R>::t *p;
+    int off;
+    __device__ __forceinline__ typename V4T<R>::t operator()(int j) const { return p[j - off]; }
+};
+
+// Force, u and w sums of slot i over its neighbour list (Fig. 2): TP lanes per particle, lane lt
+// takes neighbours lt, lt + TP, ...; the next four indices are prefetched while four pairs are
+// evaluated.
+template <bool NC> __device__ __forceinline__ int ld_idx(const int *p) {
+    if (NC) return __ldg(p);
+    return *p;
+}
+
+// NC: the list may be read through the non-coherent read-only path (it was written by an
+// earlier kernel); false when the same kernel has just built it.
+template <typename R, int TP, bool SINGLE, typename Src, bool NC = true>
+__device__ __forceinline__ void force_sum(const StepArgs<R> &a, const Src &P4, int i,
+                                          const typename V4T<R>::t &ri, int ti, const Frame<R> &F,
+                                          int lt, const typename Coef4<R>::t *s_c0,
+                                          const typename Coef2<R>::t *s_c1, R &fx, R &fy, R &fz,
+                                          R &u, R &w) {
+    typedef typename V4T<R>::t V4;
+    const typename Coef4<R>::t c1 = s_c0[0];
+    const typename Coef2<R>::t c1b = s_c1[0];
+    const int nn = a.nnb[i];
+    // sliced column-major list: neighbour k of slot i at ((i/32)*nmax + k)*32 + i%32
+    const int stride = TP * 32;
+    const int *q = a.nbl + nbl_offset(i, lt, a.nmax);
+    int k = lt;
+    int j0 = 0, j1 = 0, j2 = 0, j3 = 0;
+    if (k + 3 * TP < nn) {
+        j0 = ld_idx<NC>(q); j1 = ld_idx<NC>(q + stride); j2 = ld_idx<NC>(q + 2 * stride); j3 = ld_idx<NC>(q + 3 * stride);
+    }
+    for (; k + 3 * TP < nn; k += 4 * TP) {
+        const V4 r0 = P4(j0), r1 = P4(j1), r2 = P4(j2), r3 = P4(j3);
+        q += 4 * stride;
+        if (k + 7 * TP < nn) {   // prefetch the next four indices (Sec. 5 prefetching)
+            j0 = ld_idx<NC>(q); j1 = ld_idx<NC>(q + stride); j2 = ld_idx<NC>(q + 2 * stride);
+            j3 = ld_idx<NC>(q + 3 * stride);
+        }
+        interact<R, SINGLE>(ri, ti, r0, F, a.ntypes, s_c0, s_c1, c1, c1b, fx, fy, fz, u, w);
+        interact<R, SINGLE>(ri, ti, r1, F, a.ntypes, s_c0, s_c1, c1, c1b, fx, fy, fz, u, w);
+        interact<R, SINGLE>(ri, ti, r2, F, a.ntypes, s_c0, s_c1, c1, c1b, fx, fy, fz, u, w);
+        interact<R, SINGLE>(ri, ti, r3, F, a.ntypes, s_c0, s_c1, c1, c1b, fx, fy, fz, u, w);
+    }
+    for (; k < nn; k += TP) {
+        const int j = ld_idx<NC>(q);
+        q += stride;
+        interact<R, SINGLE>(ri, ti, P4(j), F, a.ntypes, s_c0, s_c1, c1, c1b, fx, fy, fz, u, w);
+    }
+}
+
+// Merge the TP partial sums of each particle (replaces the serial shared-memory sum of Fig. 2).
+template <typename R, int TP>
+__device__ __forceinline__ void merge_lanes(R &fx, R &fy, R &fz, R &u, R &w) {
+#pragma unroll
+    for (int o = TP / 2; o > 0; o >>= 1) {
+        fx += __shfl_xor_sync(FULL_MASK, fx, o);
+        fy += __shfl_xor_sync(FULL_MASK, fy, o);
+        fz += __shfl_xor_sync(FULL_MASK, fz, o);
+        u += __shfl_xor_sync(FULL_MASK, u, o);
+        w += __shfl_xor_sync(FULL_MASK, w, o);
+    }
+}
+
+// Leapfrog NVE / Nose-Hoover NVT update of slot i (Sec. 2), FP64 master position with image
+// counters, new FP32 mirror, skin check (Sec. 6).  Returns the particle's kinetic energy and
+// momentum.  A, B: Nose-Hoover factors (1 - xi dt/2) and 1/(1 + xi dt/2).
+template <typename R>
+__device__ __forceinline__ bool integrate_one(const StepArgs<R> &a, const SysDesc &S, int i,
+                                              const typename V4T<R>::t &ri, R fx, R fy, R fz,
+                                              R im, R m, R A, R B, R &ke, R &px, R &py, R &pz) {
+    typedef typename V4T<R>::t V4;
+    const R dt = (R)a.dt;
+    V4 v = a.vel[i];
+    if (a.integrator == 1) {
+        v.x = (A * v.x + dt * fx * im) * B;
+        v.y = (A * v.y + dt * fy * im) * B;
+        v.z = (A * v.z + dt * fz * im) * B;
+    } else {
+        v.x += dt * fx * im;
+        v.y += dt * fy * im;
+        v.z += dt * fz * im;
+    }
+    a.vel[i] = v;
+    ke = R(0.5) * m * (v.x * v.x + v.y * v.y + v.z * v.z);
+    px = m * v.x;
+    py = m * v.y;
+    pz = m * v.z;
+    // FP64 master position, wrap and image (the mixed-precision contract).  The wrap is detected
+    // on the rounded mirror (it can only round up to L, never below 0) and decided exactly in FP64
+    // only when the mirror says the particle may have left [0, L).
+    double x = a.xd[i] + (double)(dt * v.x), y = a.yd[i] + (double)(dt * v.y),
+           z = a.zd[i] + (double)(dt * v.z);
+    const R Lr = box_L<R>(S);
+    int wx = 0, wy = 0, wz = 0;
+    if (!((R)x < Lr && (R)x >= R(0))) {
+        if (x >= S.L) { x -= S.L; wx = 1; } else if (x < 0.0) { x += S.L; wx = -1; }
+    }
+    if (!((R)y < Lr && (R)y >= R(0))) {
+        if (y >= S.L) { y -= S.L; wy = 1; } else if (y < 0.0) { y += S.L; wy = -1; }
+    }
+    if (!((R)z < Lr && (R)z >= R(0))) {
+        if (z >= S.L) { z -= S.L; wz = 1; } else if (z < 0.0) { z += S.L; wz = -1; }
+    }
+    a.xd[i] = x;
+    a.yd[i] = y;
+    a.zd[i] = z;
+    if (wx | wy | wz) {
+        int4 g = a.img[i];
+        g.x += wx; g.y += wy; g.z += wz;
+        a.img[i] = g;
+    }
+    const R lim = (R)(0.25 * S.L);   // runaway / non-finite displacement
+    if (!(fabs(dt * v.x) < lim && fabs(dt * v.y) < lim && fabs(dt * v.z) < lim)) {
+        atomicExch(&a.ctrl->unstable, 1);
+        atomicExch(&a.ctrl->halt, 1);
+    }
+    const V4 rn = make_v4((R)x, (R)y, (R)z, ri.w);
+    a.pos_out[i] = rn;
+    const V4 pb = a.pos_build[i];
+    const R L = box_L<R>(S), invL = box_invL<R>(S);
+    const R bx = min_image_fast(rn.x - pb.x, L, invL);
+    const R by = min_image_fast(rn.y - pb.y, L, invL);
+    const R bz = min_image_fast(rn.z - pb.z, L, invL);
+    return (bx * bx + by * by + bz * bz) > a.half_skin2;
+}
+
+// Sum of one tile's per-particle values: within a warp in R, across the tile's warps in FP64 in
+// warp order; a tile is `tw` consecutive warps of the block (tw = blockDim/32 in the grid kernel).
+// Thread (k, q), k < tiles in the block, writes quantity q of tile k to out[k * MD_NRED + q].
+// Call with the whole block.
+template <typename R>
+__device__ __forceinline__ void tile_partial(R vals[MD_NRED], double (*s_tmp)[MD_NRED],
+                                             double *out, int tw) {
+#pragma unroll
+    for (int q2 = 0; q2 < MD_NRED; ++q2)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) vals[q2] += __shfl_down_sync(FULL_MASK, vals[q2], o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int q2 = 0; q2 < MD_NRED; ++q2) s_tmp[warp][q2] = (double)vals[q2];
+    __syncthreads();
+    const int ntile = nw / tw;
+    if (threadIdx.x < ntile * MD_NRED) {
+        const int k = threadIdx.x / MD_NRED, q = threadIdx.x % MD_NRED;
+        double acc = 0.0;
+        for (int ww = k * tw; ww < (k + 1) * tw; ++ww) acc += s_tmp[ww][q];
+        out[k * MD_NRED + q] = acc;
+    }
+}
+
+// Replica sums over its tile partials (fixed order for a fixed blockDim), thermostat carry,
+// per-step log row and the rebuild flag of the next step.  Call with the whole block.
+// Threads below nthr take tiles tt = thread, thread + nthr, ...; the others add exact zeros, so a
+// larger block reproduces the grid kernel's tree (nthr = its blockDim) bit for bit.
+template <typename R>
+__device__ __forceinline__ void replica_finish(const StepArgs<R> &a, int r, const SysDesc &S,
+                                               const double *partial, double xi, int moved,
+                                               double (*s_tmp)[MD_NRED], double *s_red,
+                                               bool from_global, int nthr) {
+    double acc[MD_NRED];
+#pragma unroll
+    for (int q2 = 0; q2 < MD_NRED; ++q2) acc[q2] = 0.0;
+    for (int tt = threadIdx.x; threadIdx.x < nthr && tt < S.ntiles; tt += nthr) {
+        const double *pp = partial + (long long)tt * MD_NRED;
+#pragma unroll
+        for (int q2 = 0; q2 < MD_NRED; ++q2) acc[q2] += from_global ? __ldcg(pp + q2) : pp[q2];
+    }
+    block_reduce_nred(acc, s_tmp, s_red);
+    if (threadIdx.x == 0) {
+        Thermo *T = a.th + r;
+        const double U = s_red[0], W = s_red[1], K = s_red[2];
+        T->U = U;
+        T->W = W;
+        T->K_minus = T->K_prev;
+        T->K_plus = K;
+        T->xi = xi;
+        T->px = s_red[3];
+        T->py = s_red[4];
+        T->pz = s_red[5];
+        T->xi_int += xi * a.dt;
+        T->xi_prev = xi;
+        T->K_prev = K;
+        const long long n = T->step;
+        T->step = n + 1;
+        if (a.log != nullptr && a.log_cap > 0) {
+            double *row = a.log + ((long long)(n % a.log_cap) * a.nrep + r) * MD_LOG_COLS;
+            const double Kn = 0.5 * (T->K_minus + K);
+            double H = U + Kn;
+            if (a.integrator == 1) {
+                const double g = 2.0 * S.K0 / a.T0;
+                H += g * a.T0 * (0.5 * xi * xi / a.inv_tau2 + T->xi_int);
+            }
+            row[0] = (double)n; row[1] = U; row[2] = W; row[3] = T->K_minus; row[4] = K;
+            row[5] = xi; row[6] = T->xi_int; row[7] = H; row[8] = s_red[3]; row[9] = s_red[4];
+            row[10] = s_red[5];
+        }
+        a.need_out[r] = moved;
+    }
+}
+
+// Nose-Hoover friction of this step from the previous step's carry (one thread).
+template <typename R>
+__device__ __forceinline__ double step_xi(const StepArgs<R> &a, const SysDesc &S, int r) {
+    if (a.integrator != 1 || a.force_only) return 0.0;
+    const Thermo *T = a.th + r;
+    return T->xi_prev + a.dt * (T->K_prev / S.K0 - 1.0) * a.inv_tau2;
+}
+
+template <typename R>
+__device__ __forceinline__ void load_tables(const StepArgs<R> &a, typename Coef4<R>::t *s_c0,
+                                            typename Coef2<R>::t *s_c1, R *s_im, R *s_m) {
+    const int npair = a.ntypes * a.ntypes;
+    for (int p = threadIdx.x; p < npair; p += blockDim.x) {
+        s_c0[p] = coef0_of<R>(a.tab[p]);
+        s_c1[p] = coef1_of<R>(a.tab[p]);
+    }
+    if (threadIdx.x < MD_MAX_TYPES) {
+        s_im[threadIdx.x] = (R)a.inv_mass[threadIdx.x];
+        s_m[threadIdx.x] = (R)a.mass[threadIdx.x];
+    }
+}
+
+// The last block of a launch closes the step: OR of the next step's rebuild flags, step counter,
+// IF-node condition of the next graph step.  Call with the whole block after s_glast is known.
+template <typename R> __device__ __forceinline__ void close_step(const StepArgs<R> &a) {
+    __threadfence();
+    int any = 0;
+    for (int rr = threadIdx.x; rr < a.nrep; rr += blockDim.x) any |= __ldcg(a.need_out + rr);
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) {
+        a.ctrl->need_any = any;
+        a.ctrl->global_ticket = 0u;
+        a.ctrl->q1 = 0;
+        a.ctrl->q2 = 0;
+        a.ctrl->step += 1;
+        if (a.has_next) cudaGraphSetConditional(a.next_handle, (any && !a.ctrl->halt) ? 1u : 0u);
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Grid step kernel (any replica size).  One CTA = one tile of (blockDim / TP) particles of one
+// replica; the last tile of a replica reduces its tile partials, the last replica closes the step.
+// ------------------------------------------------------------------------------------------------
+// STAGE: the CTA first copies its replica's positions into shared memory and gathers the
+// neighbour positions from there (replicas that fit; the copy is repeated by every tile of the
+// replica and is served from L2).
+template <typename R, int TP, bool SINGLE, bool STAGE = false>
+__global__ void __launch_bounds__(1024) k_step(const StepArgs<R> a) {
+    typedef typename V4T<R>::t V4;
+    typedef typename Coef4<R>::t C4;
+    typedef typename Coef2<R>::t C2;
+    extern __shared__ __align__(16) unsigned char k_step_smem[];
+
+    __shared__ C4 s_c0[MD_MAX_PAIRS];
+    __shared__ C2 s_c1[MD_MAX_PAIRS];
+    __shared__ R s_im[MD_MAX_TYPES], s_m[MD_MAX_TYPES];
+    __shared__ double s_tmp[32][MD_NRED];
+    __shared__ double s_red[MD_NRED];
+    __shared__ double s_xi;
+    __shared__ R s_A, s_B;
+    __shared__ int s_skip, s_last, s_glast;
+
+    const int tile = blockIdx.x;
+    const int r = a.tile_rep[tile];
+    const SysDesc S = a.sys[r];
+    load_tables(a, s_c0, s_c1, s_im, s_m);
+    if (threadIdx.x == 0) {
+        // one uniform decision per block: a halt or an unrecovered list overflow stops the step
+        s_skip = *(volatile int *)&a.ctrl->halt | *(volatile int *)&a.ctrl->overflow;
+        const double xi = step_xi(a, S, r);
+        s_xi = xi;
+        s_A = (R)(1.0 - 0.5 * xi * a.dt);
+        s_B = (R)(1.0 / (1.0 + 0.5 * xi * a.dt));
+    }
+    __syncthreads();
+    if (s_skip) return;
+    V4 *s_pos = reinterpret_cast<V4 *>(k_step_smem);
+    if (STAGE) {
+        for (int k = threadIdx.x; k < S.n; k += blockDim.x) s_pos[k] = ld_nc(a.pos_in + S.off + k);
+        __syncthreads();
+    }
+
+    const int P = blockDim.x / TP;
+    const int lp = threadIdx.x / TP, lt = threadIdx.x % TP;
+    const int li = (tile - S.tile_off) * P + lp;
+    const bool active = li < S.n;
+    const int i = S.off + li;
+
+    R fx = 0, fy = 0, fz = 0, u = 0, w = 0;
+    V4 ri = make_v4(R(0), R(0), R(0), R(0));
+    int ti = 0;
+    if (active) {
+        ri = STAGE ? s_pos[li] : a.pos_in[i];
+        ti = type_of(ri);
+        const Frame<R> F = make_frame(ri, S);
+        if (STAGE) {
+            SharedPos<R> src{s_pos, S.off};
+            force_sum<R, TP, SINGLE>(a, src, i, ri, ti, F, lt, s_c0, s_c1, fx, fy, fz, u, w);
+        } else {
+            GlobalPos<R> src{a.pos_in};
+            force_sum<R, TP, SINGLE>(a, src, i, ri, ti, F, lt, s_c0, s_c1, fx, fy, fz, u, w);
+        }
+    }
+    merge_lanes<R, TP>(fx, fy, fz, u, w);
+    const bool leader = active && lt == 0;
+    u *= R(0.5);          // Fig. 2: compensate the double counting of the full list
+    w *= R(1.0 / 6.0);    // 1/2 (double counting) * 1/3 (virial)
+
+    if (a.force_only) {
+        if (leader) {
+            a.f_out[i] = make_v4(fx, fy, fz, u);
+            a.w_out[i] = w;
+        }
+        return;
+    }
+
+    const double xi = s_xi;
+    R ke = 0, px = 0, py = 0, pz = 0;
+    bool moved = false;
+    if (leader)
+        moved = integrate_one(a, S, i, ri, fx, fy, fz, s_im[ti], s_m[ti], s_A, s_B, ke, px, py,
+                              pz);
+    if (__ballot_sync(FULL_MASK, moved) != 0u && (threadIdx.x & 31) == 0) atomicOr(a.moved + r, 1);
+
+    R vals[MD_NRED] = {u * R(leader), w * R(leader), ke, px, py, pz};
+    tile_partial(vals, s_tmp, a.partial + (long long)tile * MD_NRED, blockDim.x >> 5);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned prev = atomicAdd(a.rep_ticket + r, 1u);
+        s_last = (prev == (unsigned)(S.ntiles - 1));
+    }
+    __syncthreads();
+    if (!s_last) return;
+
+    // ---- last tile of replica r: FP64 replica sums in a fixed order, thermostat carry ----
+    __threadfence();
+    const int mv = __ldcg(a.moved + r);
+    replica_finish(a, r, S, a.partial + (long long)S.tile_off * MD_NRED, xi, mv, s_tmp, s_red,
+                   true, (int)blockDim.x);
+    if (threadIdx.x == 0) {
+        a.moved[r] = 0;
+        a.rep_ticket[r] = 0u;
+        __threadfence();
+        const unsigned g = atomicAdd(&a.ctrl->global_ticket, 1u);
+        s_glast = (g == (unsigned)(a.nrep - 1));
+    }
+    __syncthreads();
+    if (!s_glast) return;
+    close_step(a);
+}
+
+}  // namespace md

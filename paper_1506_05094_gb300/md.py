@@ -49,7 +49,7 @@ class md_stats(C.Structure):
                 ("replica_rebuilds", C.c_longlong), ("overflows", C.c_longlong),
                 ("n_max", C.c_int), ("max_neighbors", C.c_int), ("tp", C.c_int),
                 ("block", C.c_int), ("reach", C.c_int), ("build_lanes", C.c_int),
-                ("path", C.c_int), ("graph_block", C.c_int),
+                ("path", C.c_int), ("rebuild_kernels", C.c_int), ("graph_block", C.c_int),
                 ("n_total", C.c_longlong), ("neighbor_entries", C.c_longlong)]
 
 
@@ -228,8 +228,8 @@ class Sim:
         _ck(lib().md_set_list_capacity(self._h, int(n_max)), "md_set_list_capacity")
 
     def set_path(self, path):
-        """'auto' / 'grid' / 'replica' (or 0 / 1 / 2)."""
-        code = {"auto": 0, "grid": 1, "replica": 2}.get(path, path)
+        """'auto' / 'grid' / 'replica' / 'staged' (or 0 / 1 / 2 / 3)."""
+        code = {"auto": 0, "grid": 1, "replica": 2, "staged": 3}.get(path, path)
         _ck(lib().md_set_path(self._h, int(code)), "md_set_path")
 
     def set_graph_block(self, steps: int):

@@ -387,15 +387,17 @@ def _traj(sts, path, steps, tuning=(1, 128, 2, 8), graph_block=20):
     return out, en, st
 
 
+@pytest.mark.parametrize("path,code", [("replica", 2), ("staged", 3)])
 @pytest.mark.parametrize("tuning", [(1, 128, 2, 8), (4, 256, 2, 32), (2, 64, 3, 8)])
-def test_replica_resident_path_bit_identical_to_grid(tuning):
-    """Same slot order, list order and reduction tree: the two kernel paths agree bit for bit
-    (NVT, 300 steps, with rebuilds inside the replica-resident kernel)."""
+def test_kernel_paths_bit_identical_to_grid(path, code, tuning):
+    """Same slot order, list order and reduction tree: the replica-resident kernel and the grid
+    kernel with staged positions agree with the grid kernel bit for bit (NVT, 300 steps, with
+    rebuilds)."""
     sts = _ensemble([512, 1000, 700, 2048, 777, 1500])
-    a, ea, sa = _traj(sts, "replica", 300, tuning)
+    a, ea, sa = _traj(sts, path, 300, tuning)
     b, eb, sb = _traj(sts, "grid", 300, tuning)
-    assert sa["path"] == 2 and sb["path"] == 1
-    assert sa["replica_rebuilds"] > len(sts)          # rebuilds happened in-kernel
+    assert sa["path"] == code and sb["path"] == 1
+    assert sa["replica_rebuilds"] > len(sts)
     for x, y in zip(a, b):
         for u, v in zip(x, y):
             np.testing.assert_array_equal(u, v)
