@@ -382,8 +382,9 @@ def main():
     nk = st1["rebuild_kernels"]
     if path == "replica":   # one replica-resident launch per step, rebuilds inside it
         gpu_launches = args.steps
-    else:                   # + arm kernel per graph, nk-kernel rebuild pass per IF body executed
-        gpu_launches = args.steps + n_graphs + nk * passes + nk * rem
+    else:   # step kernels (two per graph step when split), arm per graph, nk per rebuild pass
+        sk = st1["step_kernels"]
+        gpu_launches = sk * (args.steps - rem) + rem + n_graphs + nk * passes + nk * rem
 
     # dominant kernel: fused step kernel, plain launches with CUDA events on the sim's stream
     prof = sim.profile(50)

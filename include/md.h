@@ -92,6 +92,7 @@ typedef struct {
     int build_lanes;            /* lanes per particle in the list build */
     int path;                   /* 1 grid, 2 replica-resident, 3 grid with staged positions */
     int rebuild_kernels;        /* kernels launched per rebuild pass on the grid path */
+    int step_kernels;           /* step kernels per graph step (2: split around the rebuild) */
     int graph_block;            /* steps per captured CUDA graph (0 = plain launches) */
     long long n_total;          /* particles over all replicas */
     long long neighbor_entries; /* sum of neighbour counts at the most recent build */

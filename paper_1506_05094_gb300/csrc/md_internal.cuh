@@ -121,6 +121,8 @@ template <typename R> struct StepArgs {
     R *w_out;
     cudaGraphConditionalHandle next_handle;
     int has_next;
+    int need_filter;          // -1 all replicas; 0 / 1: only replicas whose need_in is 0 / nonzero
+    int launch_prio;          // host side: CUDA launch priority of this launch (0 = default)
 };
 
 template <typename R> struct RebuildArgs {
@@ -154,6 +156,7 @@ template <typename R> struct RebuildArgs {
     int sort_small;          // 1: one-CTA-per-replica fused sort (k_sort_small)
     int sort_nmax, sort_cmax;
     size_t sort_smem;
+    int launch_prio;         // host side: CUDA launch priority of these launches (0 = default)
     const SysDesc *sys;
     const PairTab *tab;
     int ntypes;

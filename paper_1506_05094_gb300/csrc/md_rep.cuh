@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(1024) k_rep(const StepArgs<R> a, const Rebuild
 // performs bin, exclusive scan (cellStart), slot scatter, in-cell order by user id and the gather
 // into the scratch arrays -- the work of k_bin .. k_gather in one launch.  k_build follows.
 // ------------------------------------------------------------------------------------------------
-template <typename R> __global__ void __launch_bounds__(512) k_sort_small(const RebuildArgs<R> a) {
+template <typename R> __global__ void __launch_bounds__(1024) k_sort_small(const RebuildArgs<R> a) {
     extern __shared__ __align__(16) int sm[];
     __shared__ int s_warp[32];
     if (rebuild_off(a.ctrl)) return;

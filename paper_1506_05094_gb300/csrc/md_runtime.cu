@@ -79,6 +79,9 @@ struct md_sim {
     size_t r4 = 16;   // bytes of one Real4
     Buffers b;
     cudaStream_t stream = nullptr, cap_stream = nullptr, body_stream = nullptr;
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    int prio_hi = 0, prio_lo = 0;   // launch priorities of the split step's two branches
     bool own_stream = false;
     Ctrl *h_ctrl = nullptr;  // pinned
     long long h_step = 0;    // completed steps (host view)
@@ -327,6 +330,7 @@ template <typename R> StepArgs<R> step_args(md_sim *s, int parity, int force_onl
     a.f_out = (V4 *)s->b.f_out;
     a.w_out = (R *)s->b.w_out;
     a.has_next = 0;
+    a.need_filter = -1;
     return a;
 }
 
@@ -380,9 +384,16 @@ template <typename R> RebuildArgs<R> rebuild_args(md_sim *s, int parity, const v
     return a;
 }
 
-cudaError_t do_rebuild(md_sim *s, int parity, cudaStream_t st, const void *key = nullptr) {
-    if (s->precision == MD_FP64) return launch_rebuild<double>(rebuild_args<double>(s, parity, key), st);
-    return launch_rebuild<float>(rebuild_args<float>(s, parity, key), st);
+cudaError_t do_rebuild(md_sim *s, int parity, cudaStream_t st, const void *key = nullptr,
+                       int prio = 0) {
+    if (s->precision == MD_FP64) {
+        RebuildArgs<double> a = rebuild_args<double>(s, parity, key);
+        a.launch_prio = prio;
+        return launch_rebuild<double>(a, st);
+    }
+    RebuildArgs<float> a = rebuild_args<float>(s, parity, key);
+    a.launch_prio = prio;
+    return launch_rebuild<float>(a, st);
 }
 
 bool use_rep(const md_sim *s) {
@@ -392,8 +403,11 @@ bool use_rep(const md_sim *s) {
     return s->R >= 32;   // auto: enough replicas to occupy every SM with whole replicas
 }
 
+// Graph steps are split (unflagged replicas step while flagged ones rebuild) for batches.
+bool split_steps(const md_sim *s) { return s->R >= 8 && !use_rep(s); }
+
 cudaError_t do_step(md_sim *s, int parity, cudaStream_t st, int force_only,
-                    cudaGraphConditionalHandle next = 0, int has_next = 0) {
+                    cudaGraphConditionalHandle next = 0, int has_next = 0, int filter = -1) {
     if (!force_only && use_rep(s)) {
         StepArgs<float> a = step_args<float>(s, parity, 0);
         a.has_next = 0;
@@ -405,11 +419,15 @@ cudaError_t do_step(md_sim *s, int parity, cudaStream_t st, int force_only,
         StepArgs<double> a = step_args<double>(s, parity, force_only);
         a.next_handle = next;
         a.has_next = has_next;
+        a.need_filter = filter;
+        a.launch_prio = filter == 0 ? s->prio_lo : (filter == 1 ? s->prio_hi : 0);
         return launch_step<double>(a, s->tp, s->block, s->ntiles, st);
     }
     StepArgs<float> a = step_args<float>(s, parity, force_only);
     a.next_handle = next;
     a.has_next = has_next;
+    a.need_filter = filter;
+    a.launch_prio = filter == 0 ? s->prio_lo : (filter == 1 ? s->prio_hi : 0);
     if (s->path == 3 && s->staged_ok)
         return launch_step_staged(a, s->tp, s->block, s->ntiles, s->staged_smem, st);
     return launch_step<float>(a, s->tp, s->block, s->ntiles, st);
@@ -446,15 +464,32 @@ int build_graph(md_sim *s, int p) {
     cudaStreamCaptureStatus st;
     const cudaGraphNode_t *deps = nullptr;
     size_t ndeps = 0;
-    std::vector<cudaGraphConditionalHandle> h(B);
+    std::vector<cudaGraphConditionalHandle> h(B, 0);
+    const bool split = split_steps(s);   // split steps use no IF nodes (see below)
     bool ok = cudaStreamGetCaptureInfo(s->cap_stream, &st, nullptr, &g, &deps, nullptr, &ndeps) ==
               cudaSuccess;
-    for (int k = 0; ok && k < B; ++k)
+    for (int k = 0; ok && !split && k < B; ++k)
         ok = cudaGraphConditionalHandleCreate(&h[k], g, 0, cudaGraphCondAssignDefault) ==
              cudaSuccess;
-    ok = ok && launch_arm(s->b.ctrl, h[0], s->cap_stream) == cudaSuccess;
+    ok = ok && (split || launch_arm(s->b.ctrl, h[0], s->cap_stream) == cudaSuccess);
     for (int k = 0; ok && k < B; ++k) {
         const int q = (p + k) & 1;
+        if (split) {   // branch: the replicas that keep their list step now
+            ok = cudaEventRecord(s->ev_fork, s->cap_stream) == cudaSuccess &&
+                 cudaStreamWaitEvent(s->side_stream, s->ev_fork, 0) == cudaSuccess &&
+                 do_step(s, q, s->side_stream, 0, 0, 0, 0) == cudaSuccess &&
+                 cudaEventRecord(s->ev_join, s->side_stream) == cudaSuccess;
+            if (!ok) break;
+        }
+        if (split) {
+            // with many replicas some replica rebuilds almost every step: the rebuild kernels are
+            // plain nodes of the critical branch (they exit at once when nothing is flagged), so
+            // the branch can run beside the step of the other replicas
+            ok = do_rebuild(s, q, s->cap_stream, nullptr, s->prio_hi) == cudaSuccess &&
+                 do_step(s, q, s->cap_stream, 0, 0, 0, 1) == cudaSuccess &&
+                 cudaStreamWaitEvent(s->cap_stream, s->ev_join, 0) == cudaSuccess;
+            continue;
+        }
         ok = cudaStreamGetCaptureInfo(s->cap_stream, &st, nullptr, &g, &deps, nullptr, &ndeps) ==
              cudaSuccess;
         if (!ok) break;
@@ -475,12 +510,15 @@ int build_graph(md_sim *s, int p) {
         cudaGraph_t body_out = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(s->body_stream, &body_out);
         ok = e1 == cudaSuccess && e2 == cudaSuccess;
-        ok = ok && do_step(s, q, s->cap_stream, 0, k + 1 < B ? h[k + 1] : 0, k + 1 < B) ==
-                       cudaSuccess;
+        ok = ok && do_step(s, q, s->cap_stream, 0, k + 1 < B ? h[k + 1] : 0, k + 1 < B,
+                           split ? 1 : -1) == cudaSuccess;
+        if (split) ok = ok && cudaStreamWaitEvent(s->cap_stream, s->ev_join, 0) == cudaSuccess;
     }
     cudaGraph_t out = nullptr;
     cudaError_t e = cudaStreamEndCapture(s->cap_stream, &out);
     if (!ok || e != cudaSuccess || out == nullptr) {
+        std::fprintf(stderr, "md: graph capture failed: %s\n",
+                     cudaGetErrorString(e != cudaSuccess ? e : cudaGetLastError()));
         if (out) cudaGraphDestroy(out);
         cudaGetLastError();
         return fail(s, MD_ECUDA);
@@ -635,6 +673,9 @@ void md_destroy(md_sim *s) {
     for (cudaEvent_t &e : s->ev)
         if (e) cudaEventDestroy(e);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+    if (s->side_stream) cudaStreamDestroy(s->side_stream);
+    if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+    if (s->ev_join) cudaEventDestroy(s->ev_join);
     if (s->body_stream) cudaStreamDestroy(s->body_stream);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     delete s;
@@ -803,8 +844,20 @@ int md_create(md_sim **out, int n_replicas, const int *n_particles, const double
     ok = ok && cudaMemset(b.img, 0, sizeof(int4) * N) == cudaSuccess;
     ok = ok && cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) == cudaSuccess;
     s->own_stream = ok;
-    ok = ok && cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
-    ok = ok && cudaStreamCreateWithFlags(&s->body_stream, cudaStreamNonBlocking) == cudaSuccess;
+    // capture streams: the rebuild branch and the step after it are the critical path of a
+    // split step, so they are captured at high priority and the overlapping step at low priority
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    s->prio_lo = prio_lo;
+    s->prio_hi = prio_hi;
+    ok = ok && cudaStreamCreateWithPriority(&s->cap_stream, cudaStreamNonBlocking, prio_hi) ==
+                   cudaSuccess;
+    ok = ok && cudaStreamCreateWithPriority(&s->body_stream, cudaStreamNonBlocking, prio_hi) ==
+                   cudaSuccess;
+    ok = ok && cudaStreamCreateWithPriority(&s->side_stream, cudaStreamNonBlocking, prio_lo) ==
+                   cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) == cudaSuccess;
     for (int k = 0; ok && k < 3; ++k) ok = cudaEventCreate(&s->ev[k]) == cudaSuccess;
     if (!ok) { md_destroy(s); return MD_ECUDA; }
     rc = configure_layout(s, true);
@@ -1205,6 +1258,7 @@ int md_get_stats(md_sim *s, md_stats *out) {
     out->build_lanes = s->tpb;
     out->path = use_rep(s) ? 2 : ((s->path == 3 && s->staged_ok) ? 3 : 1);
     out->rebuild_kernels = s->sort_small ? 3 : 7;   // plan, [fused sort | 5 kernels], build
+    out->step_kernels = split_steps(s) ? 2 : 1;     // per graph step
     out->graph_block = s->graph_block;
     out->n_total = s->ntot;
     out->neighbor_entries = ent;

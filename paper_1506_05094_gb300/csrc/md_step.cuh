@@ -283,6 +283,9 @@ __global__ void __launch_bounds__(1024) k_step(const StepArgs<R> a) {
 
     const int tile = blockIdx.x;
     const int r = a.tile_rep[tile];
+    // split steps: replicas that rebuild this step and those that do not run in two launches
+    // (the second overlaps the rebuild); a tile of the other class exits at once
+    if (a.need_filter >= 0 && ((a.need_in[r] != 0) != (a.need_filter != 0))) return;
     const SysDesc S = a.sys[r];
     load_tables(a, s_c0, s_c1, s_im, s_m);
     if (threadIdx.x == 0) {

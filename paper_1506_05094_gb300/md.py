@@ -49,7 +49,8 @@ class md_stats(C.Structure):
                 ("replica_rebuilds", C.c_longlong), ("overflows", C.c_longlong),
                 ("n_max", C.c_int), ("max_neighbors", C.c_int), ("tp", C.c_int),
                 ("block", C.c_int), ("reach", C.c_int), ("build_lanes", C.c_int),
-                ("path", C.c_int), ("rebuild_kernels", C.c_int), ("graph_block", C.c_int),
+                ("path", C.c_int), ("rebuild_kernels", C.c_int), ("step_kernels", C.c_int),
+                ("graph_block", C.c_int),
                 ("n_total", C.c_longlong), ("neighbor_entries", C.c_longlong)]
 
 

@@ -256,6 +256,28 @@ def test_graph_and_plain_launches_bit_identical():
     assert a[3]["U"] == b[3]["U"] and a[3]["xi"] == b[3]["xi"]
 
 
+def test_split_graph_steps_bit_identical_to_plain_launches():
+    """With many replicas each graph step forks: replicas that keep their list step while the
+    flagged ones rebuild, then the flagged ones step.  Same arithmetic, same bits as plain
+    launches (one step kernel after the rebuild)."""
+    sts = [ka(n, seed=500 + k) for k, n in enumerate([512, 700, 600, 900, 800, 650, 1000, 550,
+                                                      750, 520])]
+    outs = []
+    for gb in (20, 0):
+        with make_sim(KA, sts, integrator="nvt", dt=0.0025, T=0.8, graph_block=gb) as sim:
+            sim.set_path("grid")
+            sim.step(200)
+            st = sim.stats()
+            if gb:
+                assert st["step_kernels"] == 2
+            outs.append(([sim.get_state(r) for r in range(len(sts))],
+                         [sim.energies(r)["xi"] for r in range(len(sts))]))
+    for x, y in zip(outs[0][0], outs[1][0]):
+        for u, v in zip(x, y):
+            np.testing.assert_array_equal(u, v)
+    assert outs[0][1] == outs[1][1]
+
+
 def test_batched_replicas_equal_single_runs():
     """Replicas inside a batch follow exactly (bitwise) the trajectory they follow alone."""
     sts = [ka(n, seed=30 + k) for k, n in enumerate([512, 700, 1024, 900])]
