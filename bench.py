@@ -122,15 +122,6 @@ class Clocks:
 
 # ------------------------------------------------------------------------------ helpers
 
-def ensemble(rank: int, replicas: int | None = None):
-    wl = synth.workload("ka_ensemble512", replicas=replicas)
-    if rank:
-        sizes = [s.n for s in wl.states]
-        wl.states = [synth.ka_random_state(n, 1.2, wl.T, synth.replica_seed(1004 + 1000 * rank, r))
-                     for r, n in enumerate(sizes)]
-    return wl
-
-
 def make_sim(wl, stream, precision="mixed"):
     from paper_1506_05094_gb300 import Sim
 
@@ -337,9 +328,10 @@ def main():
     if world > 1:
         dist.barrier()
     from paper_1506_05094_gb300 import md as mdmod  # noqa: F401  (fails loudly if not built)
+    from paper_1506_05094_gb300 import replicas as rep
 
     stream = torch.cuda.Stream(device=local)
-    wl = ensemble(rank, args.replicas)
+    wl = rep.rank_ensemble(rank, args.replicas)
     n_total = wl.n_total
     sim = make_sim(wl, stream.cuda_stream)
     if args.tuning:
@@ -369,11 +361,8 @@ def main():
     barrier()
     clocks = ck.summary()
     st1 = sim.stats()
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = n_total * world * args.steps / (ms_max / 1e3)
+    ms_max = rep.max_over_ranks(ms, device="cuda")
+    value = rep.job_throughput(n_total, world, args.steps, ms_max)
     passes = st1["rebuild_passes"] - st0["rebuild_passes"]
     # graph replays: one arm kernel + gb step kernels + 6 rebuild kernels per executed IF body;
     # an odd K ends with one plain step (its 6 rebuild kernels launch and exit if not needed)
