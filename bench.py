@@ -41,6 +41,13 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 METRIC = "particle-timesteps/s (single system & batched replicas) vs plain launches, 1 GB300"
+WORKLOAD_NAMES = {
+    "ka_ensemble512": "KA ensemble: 512 replicas, N_r~U{512..4096} seed 1004, rho=1.2, "
+                      "NVT T=0.8 dt=0.0025 skin=0.3",
+    "ka8000": "KA N=8000 rho=1.2, NVT T=0.44 dt=0.0025 skin=0.3",
+    "lj131072": "LJ N=131072 fcc rho=0.8442, NVE T=0.72 dt=0.005 skin=0.3",
+    "lj1000": "LJ N=1000 fcc rho=0.8442, NVE T=0.72 dt=0.005 skin=0.3",
+}
 UNIT = "particle-steps/s"
 GRAPH_BLOCK = 100
 
@@ -304,6 +311,9 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip single-system/e2e/cpu legs")
     ap.add_argument("--replicas", type=int, default=None, help="trim the ensemble (profiling)")
     ap.add_argument("--tuning", default=None, help="tp,block,reach[,lanes]: skip the autotuner")
+    ap.add_argument("--workload", default="ka_ensemble512",
+                    choices=["ka_ensemble512", "ka8000", "lj131072", "lj1000"],
+                    help="timed workload (default: the batched ensemble)")
     ap.add_argument("--path", default=None, choices=["grid", "replica", "staged"],
                     help="force a kernel path (default: the autotuner's choice)")
     args = ap.parse_args()
@@ -331,7 +341,10 @@ def main():
     from paper_1506_05094_gb300 import replicas as rep
 
     stream = torch.cuda.Stream(device=local)
-    wl = rep.rank_ensemble(rank, args.replicas)
+    if args.workload == "ka_ensemble512":
+        wl = rep.rank_ensemble(rank, args.replicas)
+    else:
+        wl = synth.workload(args.workload)
     n_total = wl.n_total
     sim = make_sim(wl, stream.cuda_stream)
     if args.tuning:
@@ -445,8 +458,7 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
-                "config": {"workload": "KA ensemble: 512 replicas, N_r~U{512..4096} seed 1004, "
-                                       "rho=1.2, NVT T=0.8 dt=0.0025 skin=0.3",
+                "config": {"workload": WORKLOAD_NAMES[args.workload],
                            "particles_per_gpu": n_total, "replicas": len(wl.states),
                            "graph_block": gb, "tuning_tp_block_reach_lanes": list(tuning),
                            "kernel_path": path,
