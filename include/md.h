@@ -52,7 +52,9 @@ typedef enum {
     MD_ESTATE = 6      /* call out of order, e.g. md_step before md_set_state of every replica */
 } md_status;
 
-enum { MD_SHIFTED_POTENTIAL = 0 };              /* cutoff methods (Sec. 2 "Pair potentials") */
+/* cutoff methods (Sec. 2 "Pair potentials"): shift of the potential (continuous u), or shift of
+ * the force (continuous u and F: a linear term (r - rc) |F|(rc) is added to the potential) */
+enum { MD_SHIFTED_POTENTIAL = 0, MD_SHIFTED_FORCE = 1 };
 enum { MD_MIXED = 0, MD_FP64 = 1 };             /* precision modes, see md_create */
 enum { MD_NVE_LEAPFROG = 0, MD_NVT_NOSE_HOOVER = 1 };
 
@@ -111,7 +113,8 @@ typedef struct {
  *   n_particles[r] >= 2, box[r] = edge L_r > 2 (rc_max + skin) (minimum image, Sec. 4);
  *   params: n_types x n_types row-major LJ parameters (Sec. 2), symmetric, rc > 0, sigma > 0;
  *   mass: n_types masses (NULL = all 1);  skin > 0 (Sec. 4: list holds pairs with r < rc + s);
- *   cutoff_method: MD_SHIFTED_POTENTIAL;  precision: MD_MIXED (FP32 pair math and FP32
+ *   cutoff_method: MD_SHIFTED_POTENTIAL or MD_SHIFTED_FORCE (the replica-resident and staged
+ *   kernel paths support the shifted potential only);  precision: MD_MIXED (FP32 pair math and FP32
  *   per-particle accumulation; FP64 master positions, image update and energy/virial/momentum
  *   reductions) or MD_FP64 (every quantity in FP64).
  * n_types <= 8, n_replicas >= 1.  On success *out owns device memory for all replicas. */
@@ -185,12 +188,20 @@ int md_set_path(md_sim *sim, int path);
  * device-side early exit of the rebuild kernels (the baseline launch mode). */
 int md_set_graph_block(md_sim *sim, int steps);
 
-/* Parameter search of the Appendix, over the kernel path, tp, block, reach and build_lanes: short
+/* List skin s (Sec. 4): pairs within rc + s are listed and the list is rebuilt when a particle
+ * has moved more than s/2.  Changes only the work done, never the physics.  Needs
+ * L > 2 (rc_max + s) for every replica; forces a rebuild of every replica. */
+int md_set_skin(md_sim *sim, double skin);
+int md_get_skin(md_sim *sim, double *skin);
+
+/* Parameter search of the Appendix, over the kernel path, tp, block, reach and build_lanes (and
+ * the skin when flags has MD_TUNE_SKIN: 20% then 10% steps until the time stops falling): short
  * timed runs from the
  * current state (restored after every trial), single-minimum line searches with the break rules
  * of the Appendix.  cache_path (may be NULL) is a text file of tuned parameters keyed by the
  * user parameters and the GPU name; a hit skips the search.  The state is unchanged. */
-int md_autotune(md_sim *sim, const char *cache_path, int steps_per_trial);
+enum { MD_TUNE_SKIN = 1 };
+int md_autotune(md_sim *sim, const char *cache_path, int steps_per_trial, int flags);
 
 /* Runtime counters. */
 int md_get_stats(md_sim *sim, md_stats *out);

@@ -45,6 +45,9 @@ def lib():
         L.or_version.restype = C.c_int
         L.or_get_threads.restype = C.c_int
         L.or_set_threads.argtypes = [C.c_int]
+        L.or_set_cutoff.argtypes = [C.c_int]
+        L.or_set_cutoff.restype = None
+        L.or_get_cutoff.restype = C.c_int
         L.or_pair.argtypes = [C.c_double] * 4 + [d, d]
         sig_f = [C.c_int, d, i, C.c_double, C.c_int, d, d, d, d, d, d, d]
         L.or_forces.argtypes = sig_f
@@ -75,6 +78,26 @@ def _params(model):
     rc = np.ascontiguousarray(model.rc, dtype=np.float64).ravel()
     mass = np.ascontiguousarray(model.mass, dtype=np.float64).ravel()
     return int(model.n_types), eps, sig, rc, mass
+
+
+SHIFTED_POTENTIAL, SHIFTED_FORCE = 0, 1
+
+
+class cutoff:
+    """Context manager selecting the oracle's cutoff method (0 shifted potential, 1 shifted force).
+
+    The C library holds the method in a process-wide setting; this restores the previous one."""
+
+    def __init__(self, method):
+        self.method = SHIFTED_FORCE if method in ("sf", SHIFTED_FORCE) else SHIFTED_POTENTIAL
+
+    def __enter__(self):
+        self.prev = lib().or_get_cutoff()
+        lib().or_set_cutoff(self.method)
+        return self
+
+    def __exit__(self, *exc):
+        lib().or_set_cutoff(self.prev)
 
 
 def set_threads(n: int) -> None:

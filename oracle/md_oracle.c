@@ -23,6 +23,9 @@
  *
  * Readings where the paper is silent (stated once here, used consistently):
  *   u(r)   = 4 eps [(sigma/r)^12 - (sigma/r)^6],  u_SP(r) = u(r) - u(rc) for r < rc, else 0.
+ *   Shifted force (Sec. 2: "truncation plus shift of the pair force ... a linear term in the
+ *   potential"): u_SF(r) = u(r) - u(rc) + (r - rc) F(rc), |F|_SF(r) = F(r) - F(rc), with
+ *   F(r) = -u'(r), for r < rc.
  *   F_ij   = (24 eps / r^2) [2 (sigma/r)^12 - (sigma/r)^6] r_ij,  r_ij = r_i - r_j (min image,
  *            d -= L * round(d / L), round half away from zero).
  *   u_i    = 1/2 sum_j u_SP(r_ij);  w_i = 1/2 * 1/3 sum_j r_ij . F_ij;  U = sum u_i, W = sum w_i.
@@ -67,9 +70,14 @@ int or_get_threads(void) {
 }
 
 /* ---------------------------------------------------------------------------------------------
- * Pair potential (Sec. 2 "Pair potentials", LJ 12-6 with the shifted-potential cutoff).
- * Returns u_SP and the scalar fs with F_ij = fs * r_ij.  Caller guarantees r2 < rc^2.
+ * Pair potential (Sec. 2 "Pair potentials", LJ 12-6 with the shifted-potential or the
+ * shifted-force cutoff).  Returns u and the scalar fs with F_ij = fs * r_ij.  r2 < rc^2.
  * ------------------------------------------------------------------------------------------- */
+static int g_cutoff = 0;   /* 0: shifted potential, 1: shifted force */
+
+void or_set_cutoff(int method) { g_cutoff = method; }
+int or_get_cutoff(void) { return g_cutoff; }
+
 static void lj_sp(double r2, double eps, double sig, double rc, double *u, double *fs) {
     double sr2 = sig * sig / r2;
     double sr6 = sr2 * sr2 * sr2;
@@ -77,6 +85,12 @@ static void lj_sp(double r2, double eps, double sig, double rc, double *u, doubl
     double sc6 = sc2 * sc2 * sc2;
     *u = 4.0 * eps * (sr6 * sr6 - sr6) - 4.0 * eps * (sc6 * sc6 - sc6);
     *fs = 24.0 * eps * (2.0 * sr6 * sr6 - sr6) / r2;
+    if (g_cutoff == 1) {
+        double r = sqrt(r2);
+        double frc = 24.0 * eps * (2.0 * sc6 * sc6 - sc6) / rc;   /* F(rc) = -u'(rc) */
+        *u += (r - rc) * frc;
+        *fs -= frc / r;
+    }
 }
 
 /* Exported for closed-form tests: pair energy and force magnitude along r at distance r. */

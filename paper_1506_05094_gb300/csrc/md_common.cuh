@@ -70,13 +70,10 @@ template <typename R> __device__ __forceinline__ R box_invL(const SysDesc &S);
 template <> __device__ __forceinline__ float box_invL<float>(const SysDesc &S) { return S.invLf; }
 template <> __device__ __forceinline__ double box_invL<double>(const SysDesc &S) { return S.invL; }
 
-// Per type-pair coefficients in shared memory: {rc2, c12, c6, ushift} and {a12, a6}.
+// Per type-pair coefficients in shared memory: {rc2, c12, c6, ushift} and {a12, a6, fc, rc}.
 template <typename R> struct Coef4;
 template <> struct Coef4<float> { typedef float4 t; };
 template <> struct Coef4<double> { typedef double4_32a t; };
-template <typename R> struct Coef2;
-template <> struct Coef2<float> { typedef float2 t; };
-template <> struct Coef2<double> { typedef double2 t; };
 
 template <typename R> __device__ __forceinline__ typename Coef4<R>::t coef0_of(const PairTab &p);
 template <> __device__ __forceinline__ float4 coef0_of<float>(const PairTab &p) {
@@ -85,29 +82,38 @@ template <> __device__ __forceinline__ float4 coef0_of<float>(const PairTab &p) 
 template <> __device__ __forceinline__ double4_32a coef0_of<double>(const PairTab &p) {
     return make_double4_32a(p.rc2d, p.c12d, p.c6d, p.ushiftd);
 }
-template <typename R> __device__ __forceinline__ typename Coef2<R>::t coef1_of(const PairTab &p);
-template <> __device__ __forceinline__ float2 coef1_of<float>(const PairTab &p) {
-    return make_float2(p.a12, p.a6);
+template <typename R> __device__ __forceinline__ typename Coef4<R>::t coef1_of(const PairTab &p);
+template <> __device__ __forceinline__ float4 coef1_of<float>(const PairTab &p) {
+    return make_float4(p.a12, p.a6, p.fc, p.rc);
 }
-template <> __device__ __forceinline__ double2 coef1_of<double>(const PairTab &p) {
-    return make_double2(p.a12d, p.a6d);
+template <> __device__ __forceinline__ double4_32a coef1_of<double>(const PairTab &p) {
+    return make_double4_32a(p.a12d, p.a6d, p.fcd, p.rcd);
 }
 
 __device__ __forceinline__ float fast_rcp(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double fast_rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float fast_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double fast_rsqrt(double x) { return rsqrt(x); }
 
-// One pair's contribution (the fij / ComputeInteraction of Sec. 5) for LJ with shifted potential:
-// F_ij = r^-2 (a12 r^-12 - a6 r^-6) r_ij, u += c12 r^-12 - c6 r^-6 - ushift, w += r_ij . F_ij.
-template <typename R, typename C4, typename C2>
+// One pair's contribution (the fij / ComputeInteraction of Sec. 5) for LJ, shifted potential:
+// F_ij = r^-2 (a12 r^-12 - a6 r^-6) r_ij, u += c12 r^-12 - c6 r^-6 - ushift, w += r_ij . F_ij;
+// shifted force (SF) also subtracts fc / r from the scalar force and adds (r - rc) fc to u.
+// c = {rc2, c12, c6, ushift}, b = {a12, a6, fc, rc}.
+template <bool SF, typename R, typename C4, typename C2>
 __device__ __forceinline__ void lj_pair(R dx, R dy, R dz, R r2, const C4 &c, const C2 &b, R &fx,
                                         R &fy, R &fz, R &u, R &w) {
     const R r2i = fast_rcp(r2);
     const R r6i = r2i * r2i * r2i;
-    const R fs = r2i * r6i * (b.x * r6i - b.y);
+    R fs = r2i * r6i * (b.x * r6i - b.y);
+    u += r6i * (c.y * r6i - c.z) - c.w;
+    if (SF) {
+        const R ri = fast_rsqrt(r2);
+        fs -= b.z * ri;
+        u += (r2 * ri - b.w) * b.z;
+    }
     fx += fs * dx;
     fy += fs * dy;
     fz += fs * dz;
-    u += r6i * (c.y * r6i - c.z) - c.w;
     w += fs * r2;
 }
 
@@ -171,23 +177,23 @@ __device__ __forceinline__ void pair_delta(const Frame<double> &F, const double4
     dz = min_image_fast(ri.z - rj.z, F.L, F.invL);
 }
 
-template <typename R, bool SINGLE>
+template <typename R, bool SINGLE, bool SF = false>
 __device__ __forceinline__ void interact(const typename V4T<R>::t &ri, int ti,
                                          const typename V4T<R>::t &rj, const Frame<R> &F, int nt,
                                          const typename Coef4<R>::t *s_c0,
-                                         const typename Coef2<R>::t *s_c1,
+                                         const typename Coef4<R>::t *s_c1,
                                          const typename Coef4<R>::t &c1,
-                                         const typename Coef2<R>::t &c1b, R &fx, R &fy, R &fz,
+                                         const typename Coef4<R>::t &c1b, R &fx, R &fy, R &fz,
                                          R &u, R &w) {
     R dx, dy, dz;
     pair_delta(F, ri, rj, dx, dy, dz);
     const R r2 = dx * dx + dy * dy + dz * dz;
     if (SINGLE) {
-        if (r2 < c1.x) lj_pair(dx, dy, dz, r2, c1, c1b, fx, fy, fz, u, w);
+        if (r2 < c1.x) lj_pair<SF>(dx, dy, dz, r2, c1, c1b, fx, fy, fz, u, w);
     } else {
         const int p = ti * nt + type_of(rj);
         const typename Coef4<R>::t c = s_c0[p];
-        if (r2 < c.x) lj_pair(dx, dy, dz, r2, c, s_c1[p], fx, fy, fz, u, w);
+        if (r2 < c.x) lj_pair<SF>(dx, dy, dz, r2, c, s_c1[p], fx, fy, fz, u, w);
     }
 }
 

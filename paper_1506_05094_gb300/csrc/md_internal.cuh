@@ -50,9 +50,12 @@ struct Plan {
 //   u(r)   = c12 r^-12 - c6 r^-6 - ushift    (c12 = 4 eps sigma^12, c6 = 4 eps sigma^6)
 //   F_ij   = r^-2 (a12 r^-12 - a6 r^-6) r_ij (a12 = 12 c12, a6 = 6 c6)
 //   rc2    = rc^2,  thr2 = (rc + s)^2 (neighbour threshold)
+//   shifted force adds (r - rc) fc to u and removes fc / r from the scalar force, fc = |F|(rc)
 struct PairTab {
     float rc2, c12, c6, ushift, a12, a6, thr2, pad;
+    float fc, rc, padf[2];
     double rc2d, c12d, c6d, ushiftd, a12d, a6d, thr2d, padd;
+    double fcd, rcd;
 };
 
 // Per replica thermostat carry and last-step record (FP64).
@@ -122,6 +125,7 @@ template <typename R> struct StepArgs {
     cudaGraphConditionalHandle next_handle;
     int has_next;
     int need_filter;          // -1 all replicas; 0 / 1: only replicas whose need_in is 0 / nonzero
+    int cutoff;               // 0 shifted potential, 1 shifted force
     int launch_prio;          // host side: CUDA launch priority of this launch (0 = default)
 };
 

@@ -30,10 +30,10 @@ __device__ __forceinline__ void force_direct(const StepArgs<R> &a, const SysDesc
                                              int self, const typename V4T<R>::t &ri, int ti,
                                              const Frame<R> &F, int lt,
                                              const typename Coef4<R>::t *s_c0,
-                                             const typename Coef2<R>::t *s_c1, R &fx, R &fy,
+                                             const typename Coef4<R>::t *s_c1, R &fx, R &fy,
                                              R &fz, R &u, R &w) {
     const typename Coef4<R>::t c1 = s_c0[0];
-    const typename Coef2<R>::t c1b = s_c1[0];
+    const typename Coef4<R>::t c1b = s_c1[0];
     const int nc = S.nc, span = S.span, reach = S.reach;
     const int c = cell_index(ri, S);
     const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
@@ -47,7 +47,7 @@ __device__ __forceinline__ void force_direct(const StepArgs<R> &a, const SysDesc
                 const int xx = full ? ox : (cx - reach + ox + nc) % nc;
                 for (int j = s_cs[row + xx] + lt; j < s_cs[row + xx + 1]; j += TP)
                     if (j != self)
-                        interact<R, SINGLE>(ri, ti, s_pos[j], F, a.ntypes, s_c0, s_c1, c1, c1b,
+                        interact<R, SINGLE, false>(ri, ti, s_pos[j], F, a.ntypes, s_c0, s_c1, c1, c1b,
                                             fx, fy, fz, u, w);
             }
         }
@@ -93,7 +93,7 @@ template <typename R, int TP, bool SINGLE, int TPB>
 __global__ void __launch_bounds__(1024) k_rep(const StepArgs<R> a, const RebuildArgs<R> b) {
     typedef typename V4T<R>::t V4;
     typedef typename Coef4<R>::t C4;
-    typedef typename Coef2<R>::t C2;
+    typedef typename Coef4<R>::t C2;
     extern __shared__ __align__(16) unsigned char smem[];
     // dynamic shared memory: positions, cell starts/counters, per-particle cell and slot scratch,
     // tile partials

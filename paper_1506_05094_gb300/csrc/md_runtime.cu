@@ -233,7 +233,8 @@ int configure_layout(md_sim *s, bool realloc_cells) {
         int optin3 = 0;
         cudaDeviceGetAttribute(&optin3, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
         s->staged_smem = (size_t)s->rep_nmax * 16;
-        s->staged_ok = s->precision == MD_MIXED && s->staged_smem + 8192 <= (size_t)optin3 &&
+        s->staged_ok = s->precision == MD_MIXED && s->cutoff == MD_SHIFTED_POTENTIAL &&
+                       s->staged_smem + 8192 <= (size_t)optin3 &&
                        s->staged_smem <= 100 * 1024 &&
                        prepare_step_staged(s->tp, s->nt == 1, s->staged_smem) == cudaSuccess;
         cudaGetLastError();
@@ -246,7 +247,8 @@ int configure_layout(md_sim *s, bool realloc_cells) {
     // resident CTAs per SM: shared memory (plus ~8 KB static) and 64 registers x threads
     s->rep_ctas = std::max(1, std::min(per_sm / (int)(s->rep_smem + 8192),
                                        65536 / (64 * s->rep_threads)));
-    s->rep_ok = s->precision == MD_MIXED && s->rep_smem + 8192 <= (size_t)optin &&
+    s->rep_ok = s->precision == MD_MIXED && s->cutoff == MD_SHIFTED_POTENTIAL &&
+                s->rep_smem + 8192 <= (size_t)optin &&
                 (s->tpb == 8 || s->tpb == 32) &&
                 prepare_rep(s->tp, s->tpb, s->nt == 1, s->rep_smem) == cudaSuccess;
     cudaGetLastError();
@@ -263,6 +265,20 @@ int configure_layout(md_sim *s, bool realloc_cells) {
 
 // sliced layout: ceil(ntot / 32) slices of nmax x 32 entries
 size_t nbl_entries(const md_sim *s) { return (((size_t)s->ntot + 31) / 32) * 32 * (size_t)s->nmax; }
+
+// Initial list capacity (Sec. 4): 1.35 x the ideal-gas count within rc_max + skin, plus 24.
+int estimate_nmax(const md_sim *s) {
+    double est = 0.0;
+    int n_big = 0;
+    for (int r = 0; r < s->R; ++r) {
+        const double rho = s->n[r] / (s->L[r] * s->L[r] * s->L[r]);
+        const double rl = s->rc_max + s->skin;
+        est = std::max(est, rho * 4.18879020478639 * rl * rl * rl);
+        n_big = std::max(n_big, s->n[r]);
+    }
+    const int nmax = std::min((int)std::ceil(est * 1.35) + 24, n_big - 1);
+    return std::max(nmax, 1);
+}
 
 int alloc_nbl(md_sim *s) {
     dfree(s->b.nbl);
@@ -331,6 +347,7 @@ template <typename R> StepArgs<R> step_args(md_sim *s, int parity, int force_onl
     a.w_out = (R *)s->b.w_out;
     a.has_next = 0;
     a.need_filter = -1;
+    a.cutoff = s->cutoff;
     return a;
 }
 
@@ -688,7 +705,8 @@ int md_create(md_sim **out, int n_replicas, const int *n_particles, const double
     *out = nullptr;
     if (n_replicas < 1 || !n_particles || !box || !params || n_types < 1 ||
         n_types > kMaxTypes || !(skin > 0.0) || !std::isfinite(skin) ||
-        cutoff_method != MD_SHIFTED_POTENTIAL || (precision != MD_MIXED && precision != MD_FP64))
+        (cutoff_method != MD_SHIFTED_POTENTIAL && cutoff_method != MD_SHIFTED_FORCE) ||
+        (precision != MD_MIXED && precision != MD_FP64))
         return MD_EINVAL;
     double rc_max = 0.0;
     for (int a = 0; a < n_types; ++a)
@@ -744,7 +762,9 @@ int md_create(md_sim **out, int n_replicas, const int *n_particles, const double
         const double rc6 = std::pow(q.rc, 6.0);
         const double ush = c12 / (rc6 * rc6) - c6 / rc6;
         const double thr2 = (q.rc + skin) * (q.rc + skin);
+        const double fc = (12.0 * c12 / (rc6 * rc6) - 6.0 * c6 / rc6) / q.rc;   // |F|(rc)
         PairTab &t = s->tab[p];
+        t.fcd = fc; t.rcd = q.rc; t.fc = (float)fc; t.rc = (float)q.rc;
         t.rc2d = q.rc * q.rc; t.c12d = c12; t.c6d = c6; t.ushiftd = ush;
         t.a12d = 12.0 * c12; t.a6d = 6.0 * c6; t.thr2d = thr2;
         t.rc2 = (float)t.rc2d; t.c12 = (float)c12; t.c6 = (float)c6; t.ushift = (float)ush;
@@ -776,9 +796,7 @@ int md_create(md_sim **out, int n_replicas, const int *n_particles, const double
         n_big = std::max(n_big, d.n);
     }
     // Sec. 4: fixed-capacity list; start with headroom and grow x2 on overflow
-    int nmax = (int)std::ceil(nmax_est * 1.35) + 24;
-    nmax = std::min(nmax, n_big - 1);
-    s->nmax = std::max(nmax, 1);
+    s->nmax = estimate_nmax(s);
     s->tp = 1;
     s->block = 128;
     s->reach = 2;
@@ -1200,6 +1218,38 @@ int md_get_tuning(md_sim *s, int *tp, int *block, int *reach, int *build_lanes) 
     return MD_OK;
 }
 
+int md_set_skin(md_sim *s, double skin) {
+    if (!s || !(skin > 0.0) || !std::isfinite(skin)) return MD_EINVAL;
+    if (s->sticky) return s->sticky;
+    for (int r = 0; r < s->R; ++r)
+        if (!(s->L[r] > 2.0 * (s->rc_max + skin))) return MD_EINVAL;
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(s, MD_ECUDA);
+    destroy_graphs(s);
+    s->skin = skin;
+    for (int p = 0; p < s->nt * s->nt; ++p) {
+        const double rc = s->params[p].rc, thr2 = (rc + skin) * (rc + skin);
+        s->tab[p].thr2d = thr2;
+        s->tab[p].thr2 = (float)thr2;
+    }
+    if (cudaMemcpy(s->b.tab, s->tab.data(), sizeof(PairTab) * MD_MAX_PAIRS,
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(s, MD_ECUDA);
+    const int need = estimate_nmax(s);
+    if (need > s->nmax) {
+        s->nmax = need;
+        if (alloc_nbl(s)) return MD_ENOMEM;
+    }
+    int rc = configure_layout(s, true);   // cell edge follows rc_max + skin
+    if (rc) return rc == MD_ENOMEM ? MD_ENOMEM : fail(s, MD_ECUDA);
+    return request_rebuild_all(s);
+}
+
+int md_get_skin(md_sim *s, double *skin) {
+    if (!s || !skin) return MD_EINVAL;
+    *skin = s->skin;
+    return MD_OK;
+}
+
 int md_set_list_capacity(md_sim *s, int n_max) {
     if (!s || n_max < 1) return MD_EINVAL;
     if (s->sticky) return s->sticky;
@@ -1578,7 +1628,7 @@ std::string tune_key(md_sim *s) {
 }
 
 bool cache_lookup(const char *path, const std::string &key, int *tp, int *block, int *reach,
-                  int *lanes) {
+                  int *lanes, double *skin) {
     if (!path) return false;
     FILE *f = std::fopen(path, "r");
     if (!f) return false;
@@ -1587,8 +1637,9 @@ bool cache_lookup(const char *path, const std::string &key, int *tp, int *block,
     while (std::fgets(line, sizeof(line), f)) {
         char k[900];
         int a, b, c, d;
-        if (std::sscanf(line, "%899s %d %d %d %d", k, &a, &b, &c, &d) == 5 && key == k) {
-            *tp = a; *block = b; *reach = c; *lanes = d;
+        double sk = 0.0;
+        if (std::sscanf(line, "%899s %d %d %d %d %lf", k, &a, &b, &c, &d, &sk) == 6 && key == k) {
+            *tp = a; *block = b; *reach = c; *lanes = d; *skin = sk;
             found = true;   // the last entry for a key wins
         }
     }
@@ -1597,29 +1648,32 @@ bool cache_lookup(const char *path, const std::string &key, int *tp, int *block,
 }
 
 void cache_store(const char *path, const std::string &key, int tp, int block, int reach, int lanes,
-                 double ms) {
+                 double skin, double ms) {
     if (!path) return;
     FILE *f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "%s %d %d %d %d %.6f\n", key.c_str(), tp, block, reach, lanes, ms);
+    std::fprintf(f, "%s %d %d %d %d %.9g %.6f\n", key.c_str(), tp, block, reach, lanes, skin, ms);
     std::fclose(f);
 }
 
 }  // namespace
 
-extern "C" int md_autotune(md_sim *s, const char *cache_path, int steps) {
-    if (!s || steps < 2) return MD_EINVAL;
+extern "C" int md_autotune(md_sim *s, const char *cache_path, int steps, int flags) {
+    if (!s || steps < 2 || (flags & ~MD_TUNE_SKIN)) return MD_EINVAL;
     if (s->sticky) return s->sticky;
     for (char c : s->loaded)
         if (!c) return MD_ESTATE;
-    const std::string key = tune_key(s);
+    const std::string key = tune_key(s) + ((flags & MD_TUNE_SKIN) ? "|skin-tuned" : "");
     int tp = 0, block = 0, reach = 0, lanes = 0;
-    if (cache_lookup(cache_path, key, &tp, &block, &reach, &lanes) && is_pow2_tp(tp) &&
+    double cskin = 0.0;
+    if (cache_lookup(cache_path, key, &tp, &block, &reach, &lanes, &cskin) && is_pow2_tp(tp) &&
         block >= tp && block <= 1024 && block % 32 == 0 && reach >= 1 && reach <= 3 &&
-        is_pow2_tp(lanes / 10) && lanes % 10 <= 2) {
-        int e = md_set_tuning(s, tp, block, reach, lanes / 10);
-        if (e) return e;
-        return md_set_path(s, (lanes % 10 == 2 && s->rep_ok) ? 2 : 1);
+        is_pow2_tp(lanes / 10) && lanes % 10 <= 3) {
+        int e = 0;
+        if ((flags & MD_TUNE_SKIN) && cskin > 0.0 && (e = md_set_skin(s, cskin))) return e;
+        if ((e = md_set_tuning(s, tp, block, reach, lanes / 10))) return e;
+        const int path = lanes % 10;
+        return md_set_path(s, (path == 2 && s->rep_ok) || (path == 3 && s->staged_ok) ? path : 1);
     }
     size_t bytes = 0;
     md_checkpoint_size(s, &bytes);
@@ -1699,7 +1753,27 @@ extern "C" int md_autotune(md_sim *s, const char *cache_path, int steps) {
     if ((rc = md_set_tuning(s, best_tp, best_block, best_reach, best_lanes))) return rc;
     if ((rc = md_set_graph_block(s, gb_saved))) return rc;
     if ((rc = md_load_checkpoint(s, ck.data(), bytes))) return rc;
+    // phase IV (optional): the list skin, 20% steps then 10% steps around the best (Appendix)
+    if (flags & MD_TUNE_SKIN) {
+        double best_skin = s->skin;
+        for (double step : {0.2, 0.1}) {
+            for (int dir : {1, -1}) {
+                double sk = best_skin;
+                for (;;) {
+                    sk *= (1.0 + dir * step);
+                    if (md_set_skin(s, sk) != MD_OK) break;   // box too small for this skin
+                    if ((rc = trial(best_tp, best_block, best_reach, best_lanes, &t))) return rc;
+                    if (t < best) { best = t; best_skin = sk; } else break;
+                }
+            }
+        }
+        if ((rc = md_set_skin(s, best_skin))) return rc;
+        if ((rc = md_set_tuning(s, best_tp, best_block, best_reach, best_lanes))) return rc;
+        if ((rc = md_set_graph_block(s, gb_saved))) return rc;
+        if ((rc = md_load_checkpoint(s, ck.data(), bytes))) return rc;
+    }
     (void)path_saved;
-    cache_store(cache_path, key, best_tp, best_block, best_reach, best_lanes * 10 + s->path, best);
+    cache_store(cache_path, key, best_tp, best_block, best_reach, best_lanes * 10 + s->path,
+                s->skin, best);
     return MD_OK;
 }

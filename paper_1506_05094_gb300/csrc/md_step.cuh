@@ -31,15 +31,15 @@ template <bool NC> __device__ __forceinline__ int ld_idx(const int *p) {
 
 // NC: the list may be read through the non-coherent read-only path (it was written by an
 // earlier kernel); false when the same kernel has just built it.
-template <typename R, int TP, bool SINGLE, typename Src, bool NC = true>
+template <typename R, int TP, bool SINGLE, typename Src, bool NC = true, bool SF = false>
 __device__ __forceinline__ void force_sum(const StepArgs<R> &a, const Src &P4, int i,
                                           const typename V4T<R>::t &ri, int ti, const Frame<R> &F,
                                           int lt, const typename Coef4<R>::t *s_c0,
-                                          const typename Coef2<R>::t *s_c1, R &fx, R &fy, R &fz,
+                                          const typename Coef4<R>::t *s_c1, R &fx, R &fy, R &fz,
                                           R &u, R &w) {
     typedef typename V4T<R>::t V4;
     const typename Coef4<R>::t c1 = s_c0[0];
-    const typename Coef2<R>::t c1b = s_c1[0];
+    const typename Coef4<R>::t c1b = s_c1[0];
     const int nn = a.nnb[i];
     // sliced column-major list: neighbour k of slot i at ((i/32)*nmax + k)*32 + i%32
     const int stride = TP * 32;
@@ -56,15 +56,15 @@ __device__ __forceinline__ void force_sum(const StepArgs<R> &a, const Src &P4, i
             j0 = ld_idx<NC>(q); j1 = ld_idx<NC>(q + stride); j2 = ld_idx<NC>(q + 2 * stride);
             j3 = ld_idx<NC>(q + 3 * stride);
         }
-        interact<R, SINGLE>(ri, ti, r0, F, a.ntypes, s_c0, s_c1, c1, c1b, fx, fy, fz, u, w);
-        interact<R, SINGLE>(ri, ti, r1, F, a.ntypes, s_c0, s_c1, c1, c1b, fx, fy, fz, u, w);
-        interact<R, SINGLE>(ri, ti, r2, F, a.ntypes, s_c0, s_c1, c1, c1b, fx, fy, fz, u, w);
-        interact<R, SINGLE>(ri, ti, r3, F, a.ntypes, s_c0, s_c1, c1, c1b, fx, fy, fz, u, w);
+        interact<R, SINGLE, SF>(ri, ti, r0, F, a.ntypes, s_c0, s_c1, c1, c1b, fx, fy, fz, u, w);
+        interact<R, SINGLE, SF>(ri, ti, r1, F, a.ntypes, s_c0, s_c1, c1, c1b, fx, fy, fz, u, w);
+        interact<R, SINGLE, SF>(ri, ti, r2, F, a.ntypes, s_c0, s_c1, c1, c1b, fx, fy, fz, u, w);
+        interact<R, SINGLE, SF>(ri, ti, r3, F, a.ntypes, s_c0, s_c1, c1, c1b, fx, fy, fz, u, w);
     }
     for (; k < nn; k += TP) {
         const int j = ld_idx<NC>(q);
         q += stride;
-        interact<R, SINGLE>(ri, ti, P4(j), F, a.ntypes, s_c0, s_c1, c1, c1b, fx, fy, fz, u, w);
+        interact<R, SINGLE, SF>(ri, ti, P4(j), F, a.ntypes, s_c0, s_c1, c1, c1b, fx, fy, fz, u, w);
     }
 }
 
@@ -229,7 +229,7 @@ __device__ __forceinline__ double step_xi(const StepArgs<R> &a, const SysDesc &S
 
 template <typename R>
 __device__ __forceinline__ void load_tables(const StepArgs<R> &a, typename Coef4<R>::t *s_c0,
-                                            typename Coef2<R>::t *s_c1, R *s_im, R *s_m) {
+                                            typename Coef4<R>::t *s_c1, R *s_im, R *s_m) {
     const int npair = a.ntypes * a.ntypes;
     for (int p = threadIdx.x; p < npair; p += blockDim.x) {
         s_c0[p] = coef0_of<R>(a.tab[p]);
@@ -265,11 +265,11 @@ template <typename R> __device__ __forceinline__ void close_step(const StepArgs<
 // STAGE: the CTA first copies its replica's positions into shared memory and gathers the
 // neighbour positions from there (replicas that fit; the copy is repeated by every tile of the
 // replica and is served from L2).
-template <typename R, int TP, bool SINGLE, bool STAGE = false>
+template <typename R, int TP, bool SINGLE, bool STAGE = false, bool SF = false>
 __global__ void __launch_bounds__(1024) k_step(const StepArgs<R> a) {
     typedef typename V4T<R>::t V4;
     typedef typename Coef4<R>::t C4;
-    typedef typename Coef2<R>::t C2;
+    typedef typename Coef4<R>::t C2;
     extern __shared__ __align__(16) unsigned char k_step_smem[];
 
     __shared__ C4 s_c0[MD_MAX_PAIRS];
@@ -319,10 +319,12 @@ __global__ void __launch_bounds__(1024) k_step(const StepArgs<R> a) {
         const Frame<R> F = make_frame(ri, S);
         if (STAGE) {
             SharedPos<R> src{s_pos, S.off};
-            force_sum<R, TP, SINGLE>(a, src, i, ri, ti, F, lt, s_c0, s_c1, fx, fy, fz, u, w);
+            force_sum<R, TP, SINGLE, SharedPos<R>, true, SF>(a, src, i, ri, ti, F, lt, s_c0, s_c1,
+                                                             fx, fy, fz, u, w);
         } else {
             GlobalPos<R> src{a.pos_in};
-            force_sum<R, TP, SINGLE>(a, src, i, ri, ti, F, lt, s_c0, s_c1, fx, fy, fz, u, w);
+            force_sum<R, TP, SINGLE, GlobalPos<R>, true, SF>(a, src, i, ri, ti, F, lt, s_c0, s_c1,
+                                                             fx, fy, fz, u, w);
         }
     }
     merge_lanes<R, TP>(fx, fy, fz, u, w);

@@ -17,7 +17,7 @@ import numpy as np
 from .build import LIB
 
 MD_OK, MD_EINVAL, MD_ENOMEM, MD_ECUDA, MD_EUNSTABLE, MD_ETIMEOUT, MD_ESTATE = range(7)
-MD_SHIFTED_POTENTIAL = 0
+MD_SHIFTED_POTENTIAL, MD_SHIFTED_FORCE = 0, 1
 MD_MIXED, MD_FP64 = 0, 1
 MD_NVE_LEAPFROG, MD_NVT_NOSE_HOOVER = 0, 1
 LOG_COLS = ("step", "U", "W", "K_minus", "K_plus", "xi", "xi_int", "H", "px", "py", "pz")
@@ -25,7 +25,8 @@ LOG_COLS = ("step", "U", "W", "K_minus", "K_plus", "xi", "xi_int", "H", "px", "p
 # every function declared in include/md.h
 SYMBOLS = ("md_create", "md_set_integrator", "md_set_state", "md_set_stream", "md_step",
            "md_sync", "md_get_state", "md_get_energies", "md_get_forces", "md_get_neighbors",
-           "md_set_tuning", "md_get_tuning", "md_set_list_capacity", "md_set_path",
+           "md_set_tuning", "md_get_tuning", "md_set_skin", "md_get_skin", "md_set_list_capacity",
+           "md_set_path",
            "md_set_graph_block", "md_autotune",
            "md_get_stats", "md_profile", "md_set_log", "md_get_log", "md_checkpoint_size",
            "md_save_checkpoint", "md_load_checkpoint", "md_destroy", "md_strerror",
@@ -96,7 +97,9 @@ def lib():
         "md_set_list_capacity": [p, i],
         "md_set_path": [p, i],
         "md_set_graph_block": [p, i],
-        "md_autotune": [p, C.c_char_p, i],
+        "md_autotune": [p, C.c_char_p, i, i],
+        "md_set_skin": [p, d],
+        "md_get_skin": [p, pd],
         "md_get_stats": [p, C.POINTER(md_stats)],
         "md_profile": [p, i, C.POINTER(md_timing)],
         "md_set_log": [p, i],
@@ -152,7 +155,7 @@ class Sim:
     """One md_sim: R replicas of LJ particles in cubic periodic boxes (see include/md.h)."""
 
     def __init__(self, n_particles, box, eps, sigma, rc, mass=None, skin=0.3,
-                 precision: str = "mixed", stream=None):
+                 precision: str = "mixed", stream=None, cutoff: str = "sp"):
         L = lib()
         n = np.ascontiguousarray(np.atleast_1d(n_particles), dtype=np.int32)
         bx = np.ascontiguousarray(np.atleast_1d(box), dtype=np.float64)
@@ -161,7 +164,9 @@ class Sim:
         self._h = C.c_void_p()
         prec = MD_FP64 if precision in ("fp64", MD_FP64) else MD_MIXED
         _ck(L.md_create(C.byref(self._h), int(n.shape[0]), _iptr(n), _dptr(bx), nt, pairs,
-                        None if m is None else _dptr(m), float(skin), MD_SHIFTED_POTENTIAL, prec),
+                        None if m is None else _dptr(m), float(skin),
+                        MD_SHIFTED_FORCE if cutoff in ("sf", MD_SHIFTED_FORCE) else MD_SHIFTED_POTENTIAL,
+                        prec),
             "md_create")
         self.n = n.copy()
         self.box = bx.copy()
@@ -172,7 +177,7 @@ class Sim:
 
     @classmethod
     def from_model(cls, model, states_or_sizes, boxes=None, skin=0.3, precision="mixed",
-                   stream=None):
+                   stream=None, cutoff="sp"):
         """Build from a synth.PairModel and a list of synth.State (or sizes + boxes)."""
         if boxes is None:
             sizes = [s.n for s in states_or_sizes]
@@ -180,7 +185,7 @@ class Sim:
         else:
             sizes = states_or_sizes
         return cls(sizes, boxes, model.eps, model.sigma, model.rc, model.mass, skin, precision,
-                   stream)
+                   stream, cutoff)
 
     # ---- lifecycle
     def close(self):
@@ -236,10 +241,20 @@ class Sim:
     def set_graph_block(self, steps: int):
         _ck(lib().md_set_graph_block(self._h, int(steps)), "md_set_graph_block")
 
-    def autotune(self, cache_path=None, steps_per_trial: int = 100):
+    def autotune(self, cache_path=None, steps_per_trial: int = 100, tune_skin: bool = False):
         cp = None if cache_path is None else str(cache_path).encode()
-        _ck(lib().md_autotune(self._h, cp, int(steps_per_trial)), "md_autotune")
+        _ck(lib().md_autotune(self._h, cp, int(steps_per_trial), 1 if tune_skin else 0),
+            "md_autotune")
         return self.get_tuning()
+
+    def set_skin(self, skin: float):
+        _ck(lib().md_set_skin(self._h, float(skin)), "md_set_skin")
+
+    @property
+    def skin(self) -> float:
+        v = C.c_double()
+        _ck(lib().md_get_skin(self._h, C.byref(v)), "md_get_skin")
+        return v.value
 
     # ---- state
     def set_state(self, r: int, pos, types, vel, image=None):

@@ -14,13 +14,13 @@ def rel_rms(a, b):
 
 
 def make_sim(model, states, precision="mixed", skin=0.3, integrator="nve", dt=0.005, T=1.0,
-             tau=0.2, tuning=None, graph_block=None, round_vel=True):
+             tau=0.2, tuning=None, graph_block=None, round_vel=True, cutoff="sp"):
     import torch
     from paper_1506_05094_gb300 import Sim
 
     torch.cuda.set_device(0)
     sim = Sim.from_model(model, states, skin=skin, precision=precision,
-                         stream=torch.cuda.current_stream(0).cuda_stream)
+                         stream=torch.cuda.current_stream(0).cuda_stream, cutoff=cutoff)
     sim.set_integrator(integrator, dt=dt, T=T, tau=tau)
     if tuning is not None:
         sim.set_tuning(*tuning)

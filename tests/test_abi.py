@@ -56,7 +56,7 @@ def _create(L, n, box, nt=1, eps=1.0, sig=1.0, rc=2.5, skin=0.3, cutoff=0, prec=
     dict(n=[1], box=[10.0]),                  # N >= 2
     dict(n=[100], box=[5.5]),                 # L > 2 (rc + s) = 5.6 for the minimum image
     dict(n=[100], box=[10.0], skin=0.0),      # skin > 0
-    dict(n=[100], box=[10.0], cutoff=1),      # only the shifted-potential cutoff
+    dict(n=[100], box=[10.0], cutoff=2),      # shifted potential (0) or shifted force (1) only
     dict(n=[100], box=[10.0], prec=7),        # precision mode
     dict(n=[100], box=[10.0], nt=9),          # at most 8 types
     dict(n=[100], box=[10.0], sig=-1.0),      # sigma > 0

@@ -463,3 +463,60 @@ def test_replica_resident_matches_oracle_trajectory():
             assert e["K_plus"] == pytest.approx(log[-1, 3], rel=2e-5)
             x, _ = sim.unwrapped(r)
             assert np.sqrt(np.mean((x - ref.pos) ** 2)) < 1e-4
+
+
+# ------------------------------------------------------------------ shifted force, skin
+
+@pytest.mark.parametrize("tp", [1, 4])
+def test_shifted_force_matches_oracle(tp):
+    st = ka(1500, seed=600)
+    with make_sim(KA, [st], cutoff="sf", tuning=(tp, 128, 2)) as sim:
+        f, u, w = sim.forces(0)
+    with oracle.cutoff("sf"):
+        fr, ur, wr, U, W = oracle.forces(f32(st.pos), st.types, st.L, KA)
+    assert rel_rms(f, fr) <= 1e-5, rel_rms(f, fr)
+    assert abs(u.sum() - U) <= 1e-6 * abs(U)
+    assert abs(w.sum() - W) <= 1e-6 * np.abs(wr).sum()
+
+
+def test_shifted_force_conserves_energy_better_than_shifted_potential():
+    """The force jump at rc is gone with the shifted force: the NVE energy spread over 2000
+    steps is smaller than with the shifted potential (LJ N = 1000)."""
+    st = synth.workload("lj1000").states[0]
+    spread = {}
+    for cut in ("sp", "sf"):
+        with make_sim(LJ, [st], cutoff=cut, integrator="nve", dt=0.005, graph_block=100) as sim:
+            sim.set_log(2000)
+            sim.step(2000)
+            E = sim.get_log(0)[:, 7] / st.n
+        spread[cut] = float(np.std(E[500:]))
+    print(f"NVE E/N std over steps 500-2000: SP {spread['sp']:.3e}, SF {spread['sf']:.3e}")
+    assert spread["sf"] < spread["sp"]
+
+
+def test_skin_change_keeps_forces_and_changes_rebuild_rate():
+    st = ka(2000, seed=610)
+    rates = {}
+    for skin in (0.2, 0.5):
+        with make_sim(KA, [st], integrator="nvt", dt=0.0025, T=0.8, graph_block=0) as sim:
+            sim.set_skin(skin)
+            assert sim.skin == pytest.approx(skin)
+            sim.step(300)
+            rates[skin] = sim.stats()["replica_rebuilds"]
+            f, u, w = sim.forces(0)
+            pos, img, vel = sim.get_state(0)
+            fr, ur, wr, U, W = oracle.forces(f32(pos), st.types, st.L, KA)
+            assert rel_rms(f, fr) <= 1e-5
+    assert rates[0.5] < rates[0.2]
+
+
+def test_autotune_with_skin_search(tmp_path):
+    st = ka(3000, seed=620)
+    with make_sim(KA, [st], integrator="nvt", dt=0.0025, T=0.8) as sim:
+        before = sim.get_state(0)
+        sim.autotune(str(tmp_path / "tune.txt"), steps_per_trial=20, tune_skin=True)
+        assert 0.05 < sim.skin < 2.0
+        after = sim.get_state(0)
+        for x, y in zip(before, after):
+            np.testing.assert_array_equal(x, y)
+        _check_forces(sim, st, KA)

@@ -282,3 +282,42 @@ def test_nose_hoover_with_huge_tau_is_nve():
     a.run(50)
     b.run(50)
     assert np.abs(a.pos - b.pos).max() < 1e-12
+
+
+# --------------------------------------------------------------------------------------------
+# Shifted-force cutoff (Sec. 2: shift of the pair force, a linear term in the potential)
+# --------------------------------------------------------------------------------------------
+
+# |F|(rc) of LJ at rc = 2.5 sigma: 24 eps (2 * 2.5^-12 - 2.5^-6) / 2.5 = -0.038999 eps / sigma
+F_RC_25 = 24.0 * (2 * 2.5 ** -12 - 2.5 ** -6) / 2.5
+
+
+def test_shifted_force_is_continuous_at_rc():
+    with oracle.cutoff("sf"):
+        u, f = oracle.pair(2.5 - 1e-9, 1.0, 1.0, 2.5)
+        assert abs(u) < 1e-9 and abs(f) < 1e-9          # both potential and force vanish at rc
+        u1, f1 = oracle.pair(1.0, 1.0, 1.0, 2.5)
+    # closed form at r = sigma: F_SF = 24 eps / sigma - F(rc); u_SF = -u(rc) + (sigma - rc) F(rc)
+    assert f1 == pytest.approx(24.0 - F_RC_25, rel=1e-12)
+    assert u1 == pytest.approx(-U_RC_25 + (1.0 - 2.5) * F_RC_25, rel=1e-12)
+
+
+def test_shifted_force_gradient_and_virial():
+    s = _ka_small()
+    with oracle.cutoff("sf"):
+        f, *_ = oracle.forces(s.pos, s.types, s.L, KA)
+        h = 1e-6
+        for i in (3, 50, 120):
+            for c in range(3):
+                p = s.pos.copy(); p[i, c] += h
+                up = oracle.forces(p, s.types, s.L, KA)[3]
+                p[i, c] -= 2 * h
+                um = oracle.forces(p, s.types, s.L, KA)[3]
+                assert -(up - um) / (2 * h) == pytest.approx(f[i, c], abs=2e-6 * max(1.0, np.abs(f[i]).max()))
+        _, _, _, U0, W = oracle.forces(s.pos, s.types, s.L, KA)
+        up = oracle.forces(s.pos * (1 + h), s.types, s.L * (1 + h), KA)[3]
+        um = oracle.forces(s.pos * (1 - h), s.types, s.L * (1 - h), KA)[3]
+        assert W == pytest.approx(-(up - um) / (2 * h) / 3.0, rel=1e-6, abs=1e-6 * abs(U0))
+    # back to shifted potential: forces differ by the F(rc) term
+    f_sp, *_ = oracle.forces(s.pos, s.types, s.L, KA)
+    assert np.abs(f_sp - f).max() > 1e-4
