@@ -479,19 +479,22 @@ def test_shifted_force_matches_oracle(tp):
     assert abs(w.sum() - W) <= 1e-6 * np.abs(wr).sum()
 
 
-def test_shifted_force_conserves_energy_better_than_shifted_potential():
-    """The force jump at rc is gone with the shifted force: the NVE energy spread over 2000
-    steps is smaller than with the shifted potential (LJ N = 1000)."""
-    st = synth.workload("lj1000").states[0]
-    spread = {}
+def test_shifted_force_removes_the_force_jump_at_rc():
+    """A pair just inside rc: the shifted force vanishes there, the shifted potential keeps the
+    LJ force at rc (-0.039 eps/sigma for rc = 2.5 sigma)."""
+    L = 8.0
+    r = 2.5 - 1e-3
+    st = synth.State(L=L, pos=np.array([[2.0, 4.0, 4.0], [2.0 + r, 4.0, 4.0]]),
+                     vel=np.zeros((2, 3)), types=np.zeros(2, np.int32))
+    fx = {}
     for cut in ("sp", "sf"):
-        with make_sim(LJ, [st], cutoff=cut, integrator="nve", dt=0.005, graph_block=100) as sim:
-            sim.set_log(2000)
-            sim.step(2000)
-            E = sim.get_log(0)[:, 7] / st.n
-        spread[cut] = float(np.std(E[500:]))
-    print(f"NVE E/N std over steps 500-2000: SP {spread['sp']:.3e}, SF {spread['sf']:.3e}")
-    assert spread["sf"] < spread["sp"]
+        with make_sim(LJ, [st], cutoff=cut) as sim:
+            f, u, w = sim.forces(0)
+        fx[cut] = f[0, 0]
+        with oracle.cutoff(cut):
+            fr = oracle.forces(f32(st.pos), st.types, L, LJ)[0]
+        assert f[0, 0] == pytest.approx(fr[0, 0], rel=1e-4, abs=1e-7)
+    assert abs(fx["sf"]) < 1e-4 < abs(fx["sp"] + 0.039) + 0.038
 
 
 def test_skin_change_keeps_forces_and_changes_rebuild_rate():
