@@ -93,6 +93,7 @@ typedef struct {
     int tp, block, reach;       /* threads per particle, threads per block, cell stencil reach */
     int build_lanes;            /* lanes per particle in the list build */
     int path;                   /* 1 grid, 2 replica-resident, 3 grid with staged positions */
+    int list_method;            /* 0 sorted cells, 1 O(N^2) scan, 2 no list */
     int rebuild_kernels;        /* kernels launched per rebuild pass on the grid path */
     int step_kernels;           /* step kernels per graph step (2: split around the rebuild) */
     int graph_block;            /* steps per captured CUDA graph (0 = plain launches) */
@@ -158,7 +159,8 @@ int md_get_forces(md_sim *sim, int replica, double *f, double *u, double *w);
 
 /* Test hook: neighbour list of replica r at its most recent build, as user indices.  counts[n];
  * nbrs (n, max_per_particle) row-major, each row in list order, unused slots -1.  Requires a
- * prior md_step or md_get_forces (the list exists only after a build). */
+ * prior md_step or md_get_forces (the list exists only after a build).  MD_ESTATE when the list
+ * method is MD_LIST_NONE (no list is kept). */
 int md_get_neighbors(md_sim *sim, int replica, int max_per_particle, int *counts, int *nbrs);
 
 /* Kernel shape: tp in {1,2,4,8,16,32} threads per particle in the force kernel (Sec. 3 t_p),
@@ -187,6 +189,14 @@ int md_set_path(md_sim *sim, int path);
 /* Steps captured per CUDA graph replay (even, >= 2), or 0 for plain kernel launches with
  * device-side early exit of the rebuild kernels (the baseline launch mode). */
 int md_set_graph_block(md_sim *sim, int steps);
+
+/* Neighbour-list method (Appendix phase I): 0 = sorted cells (Sec. 7, Fig. 4: bin, sort all
+ * particle data by cell, build over the cell stencil); 1 = O(N^2) scan of every particle of the
+ * replica (Sec. 6, Fig. 3; no sort, for small replicas); 2 = no list, every pair of the replica is
+ * evaluated each step (the paper's choice for very small systems).  All three follow the same
+ * pair rule; forces agree to FP32 summation order.  0 is the default. */
+enum { MD_LIST_CELLS = 0, MD_LIST_N2 = 1, MD_LIST_NONE = 2 };
+int md_set_list_method(md_sim *sim, int method);
 
 /* List skin s (Sec. 4): pairs within rc + s are listed and the list is rebuilt when a particle
  * has moved more than s/2.  Changes only the work done, never the physics.  Needs

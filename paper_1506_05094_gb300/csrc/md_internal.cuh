@@ -126,6 +126,7 @@ template <typename R> struct StepArgs {
     int has_next;
     int need_filter;          // -1 all replicas; 0 / 1: only replicas whose need_in is 0 / nonzero
     int cutoff;               // 0 shifted potential, 1 shifted force
+    int nolist;               // 1: no neighbour list, every pair of the replica is evaluated
     int launch_prio;          // host side: CUDA launch priority of this launch (0 = default)
 };
 
@@ -161,6 +162,7 @@ template <typename R> struct RebuildArgs {
     int sort_nmax, sort_cmax;
     size_t sort_smem;
     int launch_prio;         // host side: CUDA launch priority of these launches (0 = default)
+    int list_method;         // 0 sorted cells (Sec. 7), 1 O(N^2) scan (Sec. 6)
     const SysDesc *sys;
     const PairTab *tab;
     int ntypes;

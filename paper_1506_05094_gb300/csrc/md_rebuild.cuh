@@ -353,4 +353,61 @@ template <typename R, int TPB> __global__ void __launch_bounds__(MD_BUILD_BLOCK)
     }
 }
 
+// ------------------------------------------------------------------------------------------------
+// O(N^2) list build (Sec. 6, Fig. 3): TPB lanes per rebuilt particle scan every particle of its
+// replica in slot order (no cell sort), test the same bit-defined FP32 rule as the cell build and
+// compact the accepted slots by ballot in slot order.  The build positions are the current ones.
+// ------------------------------------------------------------------------------------------------
+template <typename R, int TPB>
+__global__ void __launch_bounds__(MD_BUILD_BLOCK) k_build_n2(const RebuildArgs<R> a) {
+    typedef typename V4T<R>::t V4;
+    if (rebuild_off(a.ctrl)) return;
+    __shared__ R s_thr[MD_MAX_PAIRS];
+    const int npair = a.ntypes * a.ntypes;
+    for (int p = threadIdx.x; p < npair; p += blockDim.x)
+        s_thr[p] = sizeof(R) == 4 ? (R)a.tab[p].thr2 : (R)a.tab[p].thr2d;
+    __syncthreads();
+    const int tot = a.plan->tot_p, nf = a.plan->nflag;
+    const int groups = gridDim.x * (blockDim.x / TPB);
+    const int lt = threadIdx.x % TPB, lane = threadIdx.x & 31;
+    const unsigned gmask = (TPB == 32) ? FULL_MASK : (((1u << TPB) - 1u) << (lane & ~(TPB - 1)));
+    const unsigned below = (1u << lane) - 1u;
+    for (int g = blockIdx.x * (blockDim.x / TPB) + threadIdx.x / TPB; g < tot; g += groups) {
+        int r, i;
+        pass_particle(a.plan_pp, a.plan_rep, nf, g, a.sys, r, i);
+        const SysDesc &S = a.sys[r];
+        const V4 ki = a.key[i];
+        const int ti = type_of(ki);
+        const R L = box_L<R>(S), invL = box_invL<R>(S);
+        int cnt = 0;
+        for (int b0 = S.off; b0 < S.off + S.n; b0 += TPB) {
+            const int j = b0 + lt;
+            bool ok = false;
+            if (j < S.off + S.n && j != i) {
+                const V4 kj = a.key[j];
+                const R dx = min_image_exact(kj.x - ki.x, L, invL);
+                const R dy = min_image_exact(kj.y - ki.y, L, invL);
+                const R dz = min_image_exact(kj.z - ki.z, L, invL);
+                ok = dist2_exact(dx, dy, dz) < s_thr[ti * a.ntypes + type_of(kj)];
+            }
+            const unsigned m = __ballot_sync(gmask, ok);
+            if (ok) {
+                const int sl = cnt + __popc(m & below);
+                if (sl < a.nmax) a.nbl[nbl_offset(i, sl, a.nmax)] = j;
+            }
+            cnt += __popc(m);
+        }
+        if (lt == 0) {
+            if (cnt > a.nmax) {
+                atomicMax(&a.ctrl->max_count, cnt);
+                atomicExch(&a.ctrl->overflow, 1);
+                cnt = a.nmax;
+            }
+            a.nnb[i] = cnt;
+            a.pos_build[i] = ki;
+            if (S.off == i) a.th[r].rebuilds += 1;
+        }
+    }
+}
+
 }  // namespace md

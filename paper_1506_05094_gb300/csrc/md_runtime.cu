@@ -62,6 +62,7 @@ struct md_sim {
     double dt = 0.005, T0 = 1.0, tau = 0.2;
     int tp = 1, block = 128, reach = 2, tpb = 8;
     int path = 0;            // 0 auto, 1 grid, 2 replica-resident
+    int list_method = 0;     // 0 sorted cells, 1 O(N^2) scan, 2 no list
     bool rep_ok = false;     // replica-resident kernel usable with the current shape
     size_t rep_smem = 0;
     int rep_threads = 512, rep_ctas = 1;
@@ -348,6 +349,7 @@ template <typename R> StepArgs<R> step_args(md_sim *s, int parity, int force_onl
     a.has_next = 0;
     a.need_filter = -1;
     a.cutoff = s->cutoff;
+    a.nolist = s->list_method == 2 ? 1 : 0;
     return a;
 }
 
@@ -386,6 +388,7 @@ template <typename R> RebuildArgs<R> rebuild_args(md_sim *s, int parity, const v
     a.nsm = s->nsm;
     a.tpb = s->tpb;
     a.sort_small = s->sort_small ? 1 : 0;
+    a.list_method = s->list_method == 1 ? 1 : 0;
     a.sort_nmax = s->rep_nmax;
     a.sort_cmax = s->rep_cmax;
     a.sort_smem = s->sort_smem;
@@ -403,6 +406,7 @@ template <typename R> RebuildArgs<R> rebuild_args(md_sim *s, int parity, const v
 
 cudaError_t do_rebuild(md_sim *s, int parity, cudaStream_t st, const void *key = nullptr,
                        int prio = 0) {
+    if (s->list_method == 2) return cudaSuccess;   // no list: nothing to rebuild
     if (s->precision == MD_FP64) {
         RebuildArgs<double> a = rebuild_args<double>(s, parity, key);
         a.launch_prio = prio;
@@ -414,14 +418,14 @@ cudaError_t do_rebuild(md_sim *s, int parity, cudaStream_t st, const void *key =
 }
 
 bool use_rep(const md_sim *s) {
-    if (!s->rep_ok) return false;
+    if (!s->rep_ok || s->list_method != 0) return false;
     if (s->path == 2) return true;
     if (s->path == 1 || s->path == 3) return false;
     return s->R >= 32;   // auto: enough replicas to occupy every SM with whole replicas
 }
 
 // Graph steps are split (unflagged replicas step while flagged ones rebuild) for batches.
-bool split_steps(const md_sim *s) { return s->R >= 8 && !use_rep(s); }
+bool split_steps(const md_sim *s) { return s->R >= 8 && !use_rep(s) && s->list_method != 2; }
 
 cudaError_t do_step(md_sim *s, int parity, cudaStream_t st, int force_only,
                     cudaGraphConditionalHandle next = 0, int has_next = 0, int filter = -1) {
@@ -445,7 +449,7 @@ cudaError_t do_step(md_sim *s, int parity, cudaStream_t st, int force_only,
     a.has_next = has_next;
     a.need_filter = filter;
     a.launch_prio = filter == 0 ? s->prio_lo : (filter == 1 ? s->prio_hi : 0);
-    if (s->path == 3 && s->staged_ok)
+    if (s->path == 3 && s->staged_ok && s->list_method != 2)
         return launch_step_staged(a, s->tp, s->block, s->ntiles, s->staged_smem, st);
     return launch_step<float>(a, s->tp, s->block, s->ntiles, st);
 }
@@ -454,7 +458,7 @@ cudaError_t do_step(md_sim *s, int parity, cudaStream_t st, int force_only,
 int build_graph(md_sim *s, int p) {
     const int B = s->graph_block;
     cudaGraph_t g = nullptr;
-    if (use_rep(s)) {   // one replica-resident launch per step: the rebuild is inside the kernel
+    if (use_rep(s) || s->list_method == 2) {   // one launch per step: rebuild inside / none
         if (cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
             return fail(s, MD_ECUDA);
         bool okr = true;
@@ -1162,6 +1166,7 @@ int md_get_neighbors(md_sim *s, int r, int maxp, int *counts, int *nbrs) {
     if (rc) return rc;
     if (!counts || maxp < 0 || (maxp > 0 && !nbrs)) return MD_EINVAL;
     if (s->sticky) return s->sticky;
+    if (s->list_method == 2) return MD_ESTATE;                  // no list is kept
     const int n = s->n[r], o = s->off[r];
     const int sl0 = o / 32, sl1 = (o + n - 1) / 32;            // slices holding the replica
     const size_t per = (size_t)32 * s->nmax;
@@ -1216,6 +1221,15 @@ int md_get_tuning(md_sim *s, int *tp, int *block, int *reach, int *build_lanes) 
     if (reach) *reach = s->reach;
     if (build_lanes) *build_lanes = s->tpb;
     return MD_OK;
+}
+
+int md_set_list_method(md_sim *s, int method) {
+    if (!s || method < 0 || method > 2) return MD_EINVAL;
+    if (s->sticky) return s->sticky;
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(s, MD_ECUDA);
+    destroy_graphs(s);
+    s->list_method = method;
+    return method == 2 ? MD_OK : request_rebuild_all(s);
 }
 
 int md_set_skin(md_sim *s, double skin) {
@@ -1307,7 +1321,8 @@ int md_get_stats(md_sim *s, md_stats *out) {
     out->reach = s->reach;
     out->build_lanes = s->tpb;
     out->path = use_rep(s) ? 2 : ((s->path == 3 && s->staged_ok) ? 3 : 1);
-    out->rebuild_kernels = s->sort_small ? 3 : 7;   // plan, [fused sort | 5 kernels], build
+    out->rebuild_kernels = s->list_method == 2 ? 0 : s->list_method == 1 ? 2 : s->sort_small ? 3 : 7;
+    out->list_method = s->list_method;
     out->step_kernels = split_steps(s) ? 2 : 1;     // per graph step
     out->graph_block = s->graph_block;
     out->n_total = s->ntot;
@@ -1668,10 +1683,11 @@ extern "C" int md_autotune(md_sim *s, const char *cache_path, int steps, int fla
     double cskin = 0.0;
     if (cache_lookup(cache_path, key, &tp, &block, &reach, &lanes, &cskin) && is_pow2_tp(tp) &&
         block >= tp && block <= 1024 && block % 32 == 0 && reach >= 1 && reach <= 3 &&
-        is_pow2_tp(lanes / 10) && lanes % 10 <= 3) {
+        is_pow2_tp(lanes / 100) && lanes % 10 <= 3 && (lanes / 10) % 10 <= 2) {
         int e = 0;
         if ((flags & MD_TUNE_SKIN) && cskin > 0.0 && (e = md_set_skin(s, cskin))) return e;
-        if ((e = md_set_tuning(s, tp, block, reach, lanes / 10))) return e;
+        if ((e = md_set_tuning(s, tp, block, reach, lanes / 100))) return e;
+        if ((e = md_set_list_method(s, (lanes / 10) % 10))) return e;
         const int path = lanes % 10;
         return md_set_path(s, (path == 2 && s->rep_ok) || (path == 3 && s->staged_ok) ? path : 1);
     }
@@ -1717,6 +1733,18 @@ extern "C" int md_autotune(md_sim *s, const char *cache_path, int steps, int fla
         if ((rc = trial(best_tp, best_block, best_reach, best_lanes, &tr))) return rc;
         s->path = tr < tg ? 2 : 1;
         best = std::min(tg, tr);
+    }
+    if (best >= 1e30 && (rc = trial(best_tp, best_block, best_reach, best_lanes, &best))) return rc;
+    // phase 0b: list method (Appendix phase I: "none" only below 5000 particles, "n2" below 50000)
+    {
+        int best_m = s->list_method;
+        for (int m : {1, 2}) {
+            if ((m == 2 && nmax_part > 5000) || (m == 1 && nmax_part > 50000)) continue;
+            if ((rc = md_set_list_method(s, m))) return rc;
+            if ((rc = trial(best_tp, best_block, best_reach, best_lanes, &t))) return rc;
+            if (t < best) { best = t; best_m = m; }
+        }
+        if ((rc = md_set_list_method(s, best_m))) return rc;
     }
     // phase I: cell stencil reach at the default kernel shape
     for (int re : {2, 1, 3}) {
@@ -1773,7 +1801,8 @@ extern "C" int md_autotune(md_sim *s, const char *cache_path, int steps, int fla
         if ((rc = md_load_checkpoint(s, ck.data(), bytes))) return rc;
     }
     (void)path_saved;
-    cache_store(cache_path, key, best_tp, best_block, best_reach, best_lanes * 10 + s->path,
-                s->skin, best);
+    // lanes, list method and kernel path share one cache field: lanes * 100 + method * 10 + path
+    cache_store(cache_path, key, best_tp, best_block, best_reach,
+                best_lanes * 100 + s->list_method * 10 + s->path, s->skin, best);
     return MD_OK;
 }

@@ -68,6 +68,23 @@ __device__ __forceinline__ void force_sum(const StepArgs<R> &a, const Src &P4, i
     }
 }
 
+// No list: every other particle of the replica, TP lanes per particle (the mode the paper uses
+// for very small systems, Appendix).
+template <typename R, int TP, bool SINGLE, bool SF, typename Src>
+__device__ __forceinline__ void force_all(const StepArgs<R> &a, const Src &P4, const SysDesc &S,
+                                          int i, const typename V4T<R>::t &ri, int ti,
+                                          const Frame<R> &F, int lt,
+                                          const typename Coef4<R>::t *s_c0,
+                                          const typename Coef4<R>::t *s_c1, R &fx, R &fy, R &fz,
+                                          R &u, R &w) {
+    const typename Coef4<R>::t c1 = s_c0[0];
+    const typename Coef4<R>::t c1b = s_c1[0];
+    for (int j = S.off + lt; j < S.off + S.n; j += TP)
+        if (j != i)
+            interact<R, SINGLE, SF>(ri, ti, P4(j), F, a.ntypes, s_c0, s_c1, c1, c1b, fx, fy, fz,
+                                    u, w);
+}
+
 // Merge the TP partial sums of each particle (replaces the serial shared-memory sum of Fig. 2).
 template <typename R, int TP>
 __device__ __forceinline__ void merge_lanes(R &fx, R &fy, R &fz, R &u, R &w) {
@@ -321,6 +338,9 @@ __global__ void __launch_bounds__(1024) k_step(const StepArgs<R> a) {
             SharedPos<R> src{s_pos, S.off};
             force_sum<R, TP, SINGLE, SharedPos<R>, true, SF>(a, src, i, ri, ti, F, lt, s_c0, s_c1,
                                                              fx, fy, fz, u, w);
+        } else if (a.nolist) {
+            GlobalPos<R> src{a.pos_in};
+            force_all<R, TP, SINGLE, SF>(a, src, S, i, ri, ti, F, lt, s_c0, s_c1, fx, fy, fz, u, w);
         } else {
             GlobalPos<R> src{a.pos_in};
             force_sum<R, TP, SINGLE, GlobalPos<R>, true, SF>(a, src, i, ri, ti, F, lt, s_c0, s_c1,

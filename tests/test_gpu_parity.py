@@ -494,8 +494,13 @@ def test_shifted_force_removes_the_force_jump_at_rc():
         with oracle.cutoff(cut):
             fr = oracle.forces(f32(st.pos), st.types, L, LJ)[0]
         assert f[0, 0] == pytest.approx(fr[0, 0], rel=1e-4, abs=1e-7)
-    assert abs(fx["sf"]) < 1e-4          # continuous force: ~0 just inside rc
-    assert abs(fx["sp"]) > 0.03           # the LJ force at rc is kept by the shifted potential
+    # shifted force: F_LJ(r) - F_LJ(rc) ~ F_LJ'(rc) (r - rc), linear in the distance to rc,
+    # F_LJ'(r) = 24 (7 / r^8 - 26 / r^14) (eps = sigma = 1)
+    slope = 24.0 * (7.0 / 2.5 ** 8 - 26.0 / 2.5 ** 14)
+    assert abs(fx["sf"]) == pytest.approx(slope * 1e-3, rel=0.01)
+    assert abs(fx["sf"]) < 0.01 * abs(fx["sp"])
+    # shifted potential: the LJ force at rc, 24 (2 / rc^13 - 1 / rc^7), is kept
+    assert abs(fx["sp"]) == pytest.approx(24.0 * (1.0 / 2.5 ** 7 - 2.0 / 2.5 ** 13), rel=0.01)
 
 
 def test_skin_change_keeps_forces_and_changes_rebuild_rate():
