@@ -49,6 +49,11 @@ def lib():
         L.or_set_cutoff.restype = None
         L.or_get_cutoff.restype = C.c_int
         L.or_pair.argtypes = [C.c_double] * 4 + [d, d]
+        L.or_coulomb_pair.argtypes = [C.c_double] * 3 + [d, d]
+        L.or_coulomb_pair.restype = None
+        L.or_set_coulomb.argtypes = [C.c_int, d, C.c_double]
+        L.or_set_coulomb.restype = None
+        L.or_get_coulomb_rc.restype = C.c_double
         sig_f = [C.c_int, d, i, C.c_double, C.c_int, d, d, d, d, d, d, d]
         L.or_forces.argtypes = sig_f
         L.or_forces_cells.argtypes = sig_f
@@ -73,6 +78,15 @@ def _p(a, ctype):
 
 
 def _params(model):
+    """Flattened LJ tables; also loads the model's Coulomb setting (charges, rc_C) into the
+    library, or switches the Coulomb term off for an uncharged model."""
+    q = getattr(model, "charge", None)
+    rcc = float(getattr(model, "rc_coulomb", 0.0) or 0.0)
+    if q is not None and rcc > 0.0:
+        qa = np.ascontiguousarray(q, dtype=np.float64).ravel()
+        lib().or_set_coulomb(int(model.n_types), _p(qa, C.c_double), rcc)
+    else:
+        lib().or_set_coulomb(0, None, 0.0)
     eps = np.ascontiguousarray(model.eps, dtype=np.float64).ravel()
     sig = np.ascontiguousarray(model.sigma, dtype=np.float64).ravel()
     rc = np.ascontiguousarray(model.rc, dtype=np.float64).ravel()
@@ -113,6 +127,18 @@ def pair(r: float, eps: float, sigma: float, rc: float):
     u, fm = C.c_double(), C.c_double()
     lib().or_pair(r, eps, sigma, rc, C.byref(u), C.byref(fm))
     return u.value, fm.value
+
+
+def coulomb_pair(r: float, qq: float, rcc: float):
+    """(u_C(r), |F|_C(r)) of the shifted-force Coulomb term for charge product qq; F > 0 repels."""
+    u, fm = C.c_double(), C.c_double()
+    lib().or_coulomb_pair(r, qq, rcc, C.byref(u), C.byref(fm))
+    return u.value, fm.value
+
+
+def _list_rc(model):
+    rc = getattr(model, "rc_list", None)
+    return np.asarray(model.rc if rc is None else rc, dtype=np.float64)
 
 
 def forces(pos, types, L, model, cells: bool = False):
@@ -183,7 +209,8 @@ def neighbors_fp64(pos, types, L, model, skin, maxn=None):
     pos = np.ascontiguousarray(pos, dtype=np.float64)
     types = np.ascontiguousarray(types, dtype=np.int32)
     n = pos.shape[0]
-    nt, _, _, rc, _ = _params(model)
+    nt = int(model.n_types)
+    rc = _list_rc(model).ravel()
     thr2 = np.ascontiguousarray((rc + skin) ** 2)
     maxn = n if maxn is None else maxn
     counts = np.zeros(n, dtype=np.int32)
@@ -196,8 +223,9 @@ def neighbors_fp64(pos, types, L, model, skin, maxn=None):
 
 
 def fp32_threshold(model, skin):
-    """(float)((rc_ab + s)^2) per type pair: the FP32 neighbour threshold."""
-    return ((np.asarray(model.rc, dtype=np.float64) + skin) ** 2).astype(np.float32).ravel()
+    """(float)((rc_ab + s)^2) per type pair: the FP32 neighbour threshold (rc_ab the pair's
+    interaction range, the Coulomb cutoff included)."""
+    return ((_list_rc(model) + skin) ** 2).astype(np.float32).ravel()
 
 
 def neighbors_fp32(posf, types, L, model, skin, maxn=None):

@@ -18,6 +18,9 @@
  *   - Brute-force Verlet neighbour sets: j is a neighbour of i iff j != i and the squared
  *     distance is strictly below (rc_ab + s)^2 (Sec. 3 and Figs. 3-4), in FP64 and in a
  *     bit-defined FP32 arithmetic.
+ *   - Optionally, a Coulomb term between charged particles cut off with the shifted-force method
+ *     (Sec. 8 "Electrostatics": the molten-salt benchmark uses Coulomb forces with a large
+ *     shifted-force cutoff instead of a mesh/Ewald method).
  *   - A textbook linked-cell FP64 force routine (Sec. 6 cell-index method, cells of edge >= rc,
  *     27-cell stencil) used only for large-N baselines; it must equal the double loop.
  *
@@ -26,6 +29,10 @@
  *   Shifted force (Sec. 2: "truncation plus shift of the pair force ... a linear term in the
  *   potential"): u_SF(r) = u(r) - u(rc) + (r - rc) F(rc), |F|_SF(r) = F(r) - F(rc), with
  *   F(r) = -u'(r), for r < rc.
+ *   Coulomb, shifted force (charges q in units of sqrt(4 pi eps0 eps sigma), as Sec. 8 states):
+ *   u_C(r) = q_a q_b [1/r - 1/rc_C + (r - rc_C)/rc_C^2],  |F|_C(r) = q_a q_b [1/r^2 - 1/rc_C^2]
+ *   for r < rc_C (the shifted-force construction above applied to u = q_a q_b / r); the LJ term
+ *   keeps its own rc_ab.
  *   F_ij   = (24 eps / r^2) [2 (sigma/r)^12 - (sigma/r)^6] r_ij,  r_ij = r_i - r_j (min image,
  *            d -= L * round(d / L), round half away from zero).
  *   u_i    = 1/2 sum_j u_SP(r_ij);  w_i = 1/2 * 1/3 sum_j r_ij . F_ij;  U = sum u_i, W = sum w_i.
@@ -51,7 +58,7 @@
 
 #define OR_MAX_TYPES 8
 
-int or_version(void) { return 3; }
+int or_version(void) { return 4; }
 
 void or_set_threads(int n) {
 #ifdef _OPENMP
@@ -93,6 +100,57 @@ static void lj_sp(double r2, double eps, double sig, double rc, double *u, doubl
     }
 }
 
+/* Coulomb shifted-force setting (Sec. 8): per-type charges and the Coulomb cutoff rc_C;
+ * rc_C <= 0 switches the term off (the default). */
+static double g_q[OR_MAX_TYPES];
+static double g_rcc = 0.0;
+
+void or_set_coulomb(int nt, const double *q, double rcc) {
+    for (int t = 0; t < OR_MAX_TYPES; ++t) g_q[t] = (q && t < nt) ? q[t] : 0.0;
+    g_rcc = (q && rcc > 0.0) ? rcc : 0.0;
+}
+double or_get_coulomb_rc(void) { return g_rcc; }
+
+static void coulomb_sf(double r2, double qq, double rcc, double *u, double *fs) {
+    double r = sqrt(r2);
+    *u = qq * (1.0 / r - 1.0 / rcc + (r - rcc) / (rcc * rcc));
+    *fs = qq * (1.0 / r2 - 1.0 / (rcc * rcc)) / r;    /* F_ij = fs * r_ij */
+}
+
+/* All pair terms between types ti, tj at squared distance r2: LJ within rc_ab, Coulomb within
+ * rc_C.  Adds to *u and *fs; returns 1 if any term is inside its cutoff. */
+static int pair_terms(double r2, int ti, int tj, int nt, const double *eps, const double *sig,
+                      const double *rc, double *u, double *fs) {
+    int p = ti * nt + tj, any = 0;
+    *u = 0.0; *fs = 0.0;
+    if (r2 < rc[p] * rc[p]) {
+        lj_sp(r2, eps[p], sig[p], rc[p], u, fs);
+        any = 1;
+    }
+    if (g_rcc > 0.0 && r2 < g_rcc * g_rcc) {
+        double uc, fc;
+        coulomb_sf(r2, g_q[ti] * g_q[tj], g_rcc, &uc, &fc);
+        *u += uc; *fs += fc;
+        any = 1;
+    }
+    return any;
+}
+
+/* Largest cutoff of any term (the linked-cell edge). */
+static double max_cutoff(int nt, const double *rc) {
+    double m = g_rcc;
+    for (int p = 0; p < nt * nt; ++p) if (rc[p] > m) m = rc[p];
+    return m;
+}
+
+/* Exported for closed-form tests: Coulomb shifted-force pair energy and force magnitude. */
+void or_coulomb_pair(double r, double qq, double rcc, double *u, double *fmag) {
+    if (r >= rcc) { *u = 0.0; *fmag = 0.0; return; }
+    double fs;
+    coulomb_sf(r * r, qq, rcc, u, &fs);
+    *fmag = fs * r;
+}
+
 /* Exported for closed-form tests: pair energy and force magnitude along r at distance r. */
 void or_pair(double r, double eps, double sig, double rc, double *u_sp, double *fmag) {
     if (r >= rc) { *u_sp = 0.0; *fmag = 0.0; return; }
@@ -113,14 +171,12 @@ static void one_particle(int i, int n, const double *pos, const int *type, doubl
     const int ti = type[i];
     for (int j = 0; j < n; ++j) {
         if (j == i) continue;
-        int p = ti * nt + type[j];
         double dx = min_image(xi - pos[3 * j], L);
         double dy = min_image(yi - pos[3 * j + 1], L);
         double dz = min_image(zi - pos[3 * j + 2], L);
         double r2 = dx * dx + dy * dy + dz * dz;
-        if (r2 < rc[p] * rc[p]) {
-            double uu, fs;
-            lj_sp(r2, eps[p], sig[p], rc[p], &uu, &fs);
+        double uu, fs;
+        if (pair_terms(r2, ti, type[j], nt, eps, sig, rc, &uu, &fs)) {
             fx += fs * dx; fy += fs * dy; fz += fs * dz;
             u += uu;
             w += fs * r2;
@@ -172,8 +228,7 @@ int or_forces_cells(int n, const double *pos, const int *type, double L, int nt,
                     const double *eps, const double *sig, const double *rc, double *f, double *u,
                     double *w, double *UW) {
     if (n < 0 || nt < 1 || nt > OR_MAX_TYPES || !(L > 0)) return 1;
-    double rcmax = 0;
-    for (int p = 0; p < nt * nt; ++p) if (rc[p] > rcmax) rcmax = rc[p];
+    double rcmax = max_cutoff(nt, rc);
     int nc = (int)floor(L / rcmax);
     if (nc < 3) return or_forces(n, pos, type, L, nt, eps, sig, rc, f, u, w, UW);
     long ncell = (long)nc * nc * nc;
@@ -202,14 +257,12 @@ int or_forces_cells(int n, const double *pos, const int *type, double L, int nt,
                         cz = (cid[3 * i + 2] + dz + nc) % nc;
                     for (int j = head[((long)cz * nc + cy) * nc + cx]; j >= 0; j = next[j]) {
                         if (j == i) continue;
-                        int p = ti * nt + type[j];
                         double ddx = min_image(xi - pos[3 * j], L);
                         double ddy = min_image(yi - pos[3 * j + 1], L);
                         double ddz = min_image(zi - pos[3 * j + 2], L);
                         double r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                        if (r2 < rc[p] * rc[p]) {
-                            double e, fs;
-                            lj_sp(r2, eps[p], sig[p], rc[p], &e, &fs);
+                        double e, fs;
+                        if (pair_terms(r2, ti, type[j], nt, eps, sig, rc, &e, &fs)) {
                             fx += fs * ddx; fy += fs * ddy; fz += fs * ddz;
                             uu += e;
                             ww += fs * r2;

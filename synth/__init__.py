@@ -75,20 +75,35 @@ def replica_seed(config_seed: int, r: int) -> int:
 
 @dataclass
 class PairModel:
-    """Per type-pair LJ parameters (symmetric n_types x n_types matrices) and per-type masses."""
+    """Per type-pair LJ parameters (symmetric n_types x n_types matrices) and per-type masses.
+
+    Optionally per-type charges with a shifted-force Coulomb cutoff rc_coulomb (charges in units
+    of sqrt(4 pi eps0 eps sigma)); charge None means no Coulomb term."""
     eps: np.ndarray
     sigma: np.ndarray
     rc: np.ndarray
     mass: np.ndarray
     name: str = ""
+    charge: np.ndarray | None = None
+    rc_coulomb: float = 0.0
 
     @property
     def n_types(self) -> int:
         return int(self.mass.shape[0])
 
     @property
+    def coulomb(self) -> bool:
+        return self.charge is not None and self.rc_coulomb > 0.0
+
+    @property
+    def rc_list(self) -> np.ndarray:
+        """Per type-pair interaction range: the larger of rc_ab and the Coulomb cutoff."""
+        rc = np.asarray(self.rc, dtype=np.float64)
+        return np.maximum(rc, self.rc_coulomb) if self.coulomb else rc
+
+    @property
     def rc_max(self) -> float:
-        return float(self.rc.max())
+        return float(self.rc_list.max())
 
 
 def lj_model(rc: float = 2.5) -> PairModel:
@@ -103,6 +118,15 @@ def ka_model(rc_factor: float = 2.5) -> PairModel:
     eps = np.array([[1.0, 1.5], [1.5, 0.5]])
     sig = np.array([[1.0, 0.8], [0.8, 0.88]])
     return PairModel(eps=eps, sigma=sig, rc=rc_factor * sig, mass=np.ones(2), name="KA")
+
+
+def salt_model(rc_lj: float = 2.5, rc_coulomb: float = 6.0) -> PairModel:
+    """Molten-salt model of the Coulomb benchmark: two species with identical LJ parameters
+    (eps = sigma = m = 1, LJ cut at rc_lj) and charges +1 / -1, Coulomb cut at rc_coulomb."""
+    one = np.ones((2, 2))
+    return PairModel(eps=one.copy(), sigma=one.copy(), rc=np.full((2, 2), rc_lj),
+                     mass=np.ones(2), name="salt", charge=np.array([1.0, -1.0]),
+                     rc_coulomb=rc_coulomb)
 
 
 # ----------------------------------------------------------------------------------------------
@@ -220,7 +244,8 @@ class Workload:
 
 
 def workload(name: str, replicas: int | None = None) -> Workload:
-    """Recipes.  Names: lj1000, ka8000, lj131072, ka_ensemble512, ka_ensemble64.
+    """Recipes.  Names: lj1000, ka8000, lj131072, ka_ensemble512, ka_ensemble64, and the
+    Coulomb (molten salt) systems salt2000, salt20000, salt100000.
 
     ``replicas`` trims a batched recipe to its first R replicas (same seeds), for small tests.
     """
@@ -250,4 +275,12 @@ def workload(name: str, replicas: int | None = None) -> Workload:
                   for r, nr in enumerate(sizes)]
         return Workload(name, m, states, integ, 0.0025, T, tau, skin,
                         100 if name == "ka_ensemble512" else 1000000)
+    if name in ("salt2000", "salt20000", "salt100000"):
+        # Coulomb benchmark state point: rho = 0.3677, T = 2, dt = 0.004, 50 % of each charge,
+        # random start on a jittered lattice (no two ions closer than 0.95 sigma)
+        n = int(name[4:])
+        m = salt_model()
+        st = ka_random_state(n, 0.3677, 2.0, 1006, frac_a=0.5, model=m, min_sep=0.95)
+        st.meta["kind"] = "salt_random"
+        return Workload(name, m, [st], "nvt", 0.004, 2.0, tau, skin, 1000)
     raise KeyError(name)

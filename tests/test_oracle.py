@@ -321,3 +321,105 @@ def test_shifted_force_gradient_and_virial():
     # back to shifted potential: forces differ by the F(rc) term
     f_sp, *_ = oracle.forces(s.pos, s.types, s.L, KA)
     assert np.abs(f_sp - f).max() > 1e-4
+
+
+# --------------------------------------------------------------------------------------------
+# Coulomb with the shifted-force cutoff (Sec. 8, molten-salt benchmark)
+# --------------------------------------------------------------------------------------------
+
+SALT = synth.salt_model()
+MADELUNG_NACL = 1.747564594633      # rock-salt Madelung constant (nearest-neighbour distance a)
+
+
+def _salt_state(n, seed=5):
+    return synth.ka_random_state(n, 0.3677, 2.0, seed, frac_a=0.5, model=SALT, min_sep=0.95)
+
+
+def test_coulomb_sf_vanishes_at_rc_and_tends_to_coulombs_law():
+    u, f = oracle.coulomb_pair(6.0 - 1e-9, -1.0, 6.0)
+    assert abs(u) < 1e-9 and abs(f) < 1e-9
+    assert oracle.coulomb_pair(6.0, 1.0, 6.0) == (0.0, 0.0)
+    for r in (0.7, 1.0, 2.0, 5.0):          # rc -> infinity: u = qq / r, F = qq / r^2
+        u, f = oracle.coulomb_pair(r, -1.0, 1e9)
+        assert u == pytest.approx(-1.0 / r, rel=1e-7)
+        assert f == pytest.approx(-1.0 / r ** 2, rel=1e-7)
+
+
+def test_opposite_charges_attract_beyond_the_lj_range():
+    """Two ions 3 sigma apart: outside the LJ cutoff (2.5), inside rc_C = 6, so the force is the
+    Coulomb one alone, pointing from + to - (attraction), |F| = 1/9 - 1/36."""
+    pos = np.array([[2.0, 7.0, 7.0], [5.0, 7.0, 7.0]])
+    f, u, w, U, W = oracle.forces(pos, np.array([0, 1], np.int32), 14.0, SALT)
+    assert f[0, 0] == pytest.approx(1.0 / 9.0 - 1.0 / 36.0, rel=1e-12)    # toward x = 5
+    assert f[1, 0] == pytest.approx(-f[0, 0], rel=1e-15)
+    assert U < 0 and np.abs(f[:, 1:]).max() == 0.0
+    same, *_ = oracle.forces(pos, np.array([0, 0], np.int32), 14.0, SALT)
+    assert same[0, 0] == pytest.approx(-f[0, 0], rel=1e-12)                # like charges repel
+
+
+def test_coulomb_force_is_minus_gradient_and_virial_is_volume_derivative():
+    s = _salt_state(1000)                    # L = 13.96 > 2 rc_C
+    f, *_ = oracle.forces(s.pos, s.types, s.L, SALT)
+    h = 1e-6
+    for i in (0, 333, 999):
+        for c in range(3):
+            p = s.pos.copy(); p[i, c] += h
+            up = oracle.forces(p, s.types, s.L, SALT)[3]
+            p[i, c] -= 2 * h
+            um = oracle.forces(p, s.types, s.L, SALT)[3]
+            assert -(up - um) / (2 * h) == pytest.approx(
+                f[i, c], abs=2e-6 * max(1.0, np.abs(f[i]).max()))
+    _, _, _, U0, W = oracle.forces(s.pos, s.types, s.L, SALT)
+    up = oracle.forces(s.pos * (1 + h), s.types, s.L * (1 + h), SALT)[3]
+    um = oracle.forces(s.pos * (1 - h), s.types, s.L * (1 - h), SALT)[3]
+    assert W == pytest.approx(-(up - um) / (2 * h) / 3.0, rel=1e-6, abs=1e-6 * abs(U0))
+    assert np.abs(f.sum(axis=0)).max() < 1e-12 * np.abs(f).sum()
+
+
+@pytest.mark.parametrize("rcc", [6.0, 6.9])
+def test_rock_salt_lattice_energy_is_madelung_plus_self_term(rcc):
+    """Rock salt (a = 1, 14^3 ions, LJ switched off): forces vanish by symmetry, and the
+    shifted-force energy per ion is the Madelung value -M/2 plus q^2/rc_C, the self term that
+    the -2/rc_C part of the pair sum leaves over a charge-neutral sphere (the ions inside rc_C
+    carry net charge ~ -q_i), up to the sphere's charge fluctuation (<= 0.01 at these rc_C).
+    A dropped linear term (plain shifted potential) moves U/N by > 0.1."""
+    k = 14
+    g = np.arange(k, dtype=np.float64)
+    X = np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1).reshape(-1, 3)
+    types = (X.sum(axis=1).astype(np.int64) % 2).astype(np.int32)
+    model = synth.PairModel(eps=np.zeros((2, 2)), sigma=np.ones((2, 2)),
+                            rc=np.full((2, 2), 2.5), mass=np.ones(2),
+                            charge=np.array([1.0, -1.0]), rc_coulomb=rcc)
+    f, u, w, U, W = oracle.forces(X + 0.5, types, float(k), model, cells=True)
+    assert np.abs(f).max() < 1e-10
+    assert np.ptp(u) < 1e-12
+    assert U / len(X) == pytest.approx(-MADELUNG_NACL / 2 + 1.0 / rcc, abs=0.01)
+
+
+def test_salt_linked_cells_equal_double_loop():
+    s = _salt_state(3000, seed=9)            # L = 20.1: three cells of edge >= rc_C per side
+    a = oracle.forces(s.pos, s.types, s.L, SALT)
+    b = oracle.forces(s.pos, s.types, s.L, SALT, cells=True)
+    np.testing.assert_allclose(b[0], a[0], rtol=0, atol=1e-11 * np.abs(a[0]).max())
+    assert b[3] == pytest.approx(a[3], rel=1e-12)
+    assert b[4] == pytest.approx(a[4], rel=1e-12)
+
+
+def test_salt_nve_conserves_energy():
+    """SF Coulomb + shifted-potential LJ over 300 steps at dt = 0.004: the total energy
+    fluctuates far less than the potential energy (a force inconsistent with U would drift)."""
+    s = _salt_state(1000, seed=11)
+    run = oracle.Run(s.pos, s.vel, s.types, s.L, SALT, "nve", 0.004)
+    run.run(100)                                     # leave the lattice start
+    log = run.run(300)
+    H, U = log[:, 9], log[:, 0]
+    assert np.ptp(H) < 0.02 * np.ptp(U)
+    assert np.abs(log[:, 6:9]).max() < 1e-10 * s.n
+
+
+def test_salt_neighbour_count_matches_density():
+    """The list range is rc_C + s: about rho 4/3 pi (rc_C + s)^3 ~ 385 neighbours per ion."""
+    s = _salt_state(2000, seed=12)
+    _, counts = oracle.neighbors_fp64(s.pos, s.types, s.L, SALT, 0.3, maxn=1)
+    expect = 0.3677 * 4.0 / 3.0 * math.pi * 6.3 ** 3
+    assert counts.mean() == pytest.approx(expect, rel=0.03)
