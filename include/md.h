@@ -198,6 +198,17 @@ int md_set_graph_block(md_sim *sim, int steps);
 enum { MD_LIST_CELLS = 0, MD_LIST_N2 = 1, MD_LIST_NONE = 2 };
 int md_set_list_method(md_sim *sim, int method);
 
+/* Shifted-force Coulomb term between charged particles (Sec. 8, the molten-salt benchmark: Coulomb
+ * forces with a large shifted-force cutoff instead of a mesh method).  charge[n_types] in units of
+ * sqrt(4 pi eps0 eps sigma) (the paper's reduced units), rc_coulomb the Coulomb cutoff rc_C:
+ *   u_C(r) = q_a q_b (1/r - 1/rc_C + (r - rc_C)/rc_C^2),  F_ij = q_a q_b (1/r^2 - 1/rc_C^2) r_ij/r
+ * for r < rc_C, added to the LJ term (which keeps its own rc_ab and cutoff method).  The list
+ * range of every pair becomes max(rc_ab, rc_C) + s.  charge NULL switches the term off.  Needs
+ * L > 2 (max(rc_max, rc_C) + s); MD_EINVAL otherwise, or for rc_coulomb <= 0 with charges, or a
+ * non-finite charge (no state change).  Forces a rebuild of every replica; the Coulomb term runs
+ * on the grid kernel path (paths 2 and 3 are not used while it is on). */
+int md_set_coulomb(md_sim *sim, const double *charge, double rc_coulomb);
+
 /* List skin s (Sec. 4): pairs within rc + s are listed and the list is rebuilt when a particle
  * has moved more than s/2.  Changes only the work done, never the physics.  Needs
  * L > 2 (rc_max + s) for every replica; forces a rebuild of every replica. */

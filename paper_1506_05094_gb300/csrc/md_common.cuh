@@ -90,6 +90,14 @@ template <> __device__ __forceinline__ double4_32a coef1_of<double>(const PairTa
     return make_double4_32a(p.a12d, p.a6d, p.fcd, p.rcd);
 }
 
+template <typename R> __device__ __forceinline__ typename Coef4<R>::t coef2_of(const PairTab &p);
+template <> __device__ __forceinline__ float4 coef2_of<float>(const PairTab &p) {
+    return make_float4(p.qrc2, p.qq, p.qf, p.qu);
+}
+template <> __device__ __forceinline__ double4_32a coef2_of<double>(const PairTab &p) {
+    return make_double4_32a(p.qrc2d, p.qqd, p.qfd, p.qud);
+}
+
 __device__ __forceinline__ float fast_rcp(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double fast_rcp(double x) { return 1.0 / x; }
 __device__ __forceinline__ float fast_rsqrt(float x) { return rsqrtf(x); }
@@ -111,6 +119,21 @@ __device__ __forceinline__ void lj_pair(R dx, R dy, R dz, R r2, const C4 &c, con
         fs -= b.z * ri;
         u += (r2 * ri - b.w) * b.z;
     }
+    fx += fs * dx;
+    fy += fs * dy;
+    fz += fs * dz;
+    w += fs * r2;
+}
+
+// Shifted-force Coulomb term (Sec. 8, molten salt) for r < rc_C:
+// u = qq (1/r - 2/rc_C + r/rc_C^2), F_ij = (qq/r) (1/r^2 - 1/rc_C^2) r_ij.
+// q = {rc_C^2, qq, qq / rc_C^2, 2 qq / rc_C}.
+template <typename R, typename C4>
+__device__ __forceinline__ void coulomb_pair(R dx, R dy, R dz, R r2, const C4 &q, R &fx, R &fy,
+                                             R &fz, R &u, R &w) {
+    const R ri = fast_rsqrt(r2);
+    const R fs = ri * (q.y * ri * ri - q.z);
+    u += q.y * ri - q.w + q.z * (r2 * ri);
     fx += fs * dx;
     fy += fs * dy;
     fz += fs * dz;
@@ -177,14 +200,20 @@ __device__ __forceinline__ void pair_delta(const Frame<double> &F, const double4
     dz = min_image_fast(ri.z - rj.z, F.L, F.invL);
 }
 
-template <typename R, bool SINGLE, bool SF = false>
+// Potential kind (template POT, a bit set): bit 0 = LJ with the shifted-force cutoff (else
+// shifted potential), bit 1 = shifted-force Coulomb term (s_cq holds its coefficients; only
+// with per-pair tables, SINGLE = false).
+template <typename R, bool SINGLE, int POT = 0>
 __device__ __forceinline__ void interact(const typename V4T<R>::t &ri, int ti,
                                          const typename V4T<R>::t &rj, const Frame<R> &F, int nt,
                                          const typename Coef4<R>::t *s_c0,
                                          const typename Coef4<R>::t *s_c1,
                                          const typename Coef4<R>::t &c1,
                                          const typename Coef4<R>::t &c1b, R &fx, R &fy, R &fz,
-                                         R &u, R &w) {
+                                         R &u, R &w,
+                                         const typename Coef4<R>::t *s_cq = nullptr) {
+    static_assert(!(SINGLE && (POT & 2)), "the Coulomb term needs the per-pair tables");
+    constexpr bool SF = (POT & 1) != 0;
     R dx, dy, dz;
     pair_delta(F, ri, rj, dx, dy, dz);
     const R r2 = dx * dx + dy * dy + dz * dz;
@@ -194,6 +223,10 @@ __device__ __forceinline__ void interact(const typename V4T<R>::t &ri, int ti,
         const int p = ti * nt + type_of(rj);
         const typename Coef4<R>::t c = s_c0[p];
         if (r2 < c.x) lj_pair<SF>(dx, dy, dz, r2, c, s_c1[p], fx, fy, fz, u, w);
+        if (POT & 2) {
+            const typename Coef4<R>::t q = s_cq[p];
+            if (r2 < q.x) coulomb_pair(dx, dy, dz, r2, q, fx, fy, fz, u, w);
+        }
     }
 }
 

@@ -56,6 +56,9 @@ struct PairTab {
     float fc, rc, padf[2];
     double rc2d, c12d, c6d, ushiftd, a12d, a6d, thr2d, padd;
     double fcd, rcd;
+    // shifted-force Coulomb (Sec. 8): rc_C^2, q_a q_b, q_a q_b / rc_C^2, 2 q_a q_b / rc_C
+    float qrc2, qq, qf, qu;
+    double qrc2d, qqd, qfd, qud;
 };
 
 // Per replica thermostat carry and last-step record (FP64).
@@ -126,6 +129,7 @@ template <typename R> struct StepArgs {
     int has_next;
     int need_filter;          // -1 all replicas; 0 / 1: only replicas whose need_in is 0 / nonzero
     int cutoff;               // 0 shifted potential, 1 shifted force
+    int coulomb;              // 1: shifted-force Coulomb term between charged types
     int nolist;               // 1: no neighbour list, every pair of the replica is evaluated
     int launch_prio;          // host side: CUDA launch priority of this launch (0 = default)
 };

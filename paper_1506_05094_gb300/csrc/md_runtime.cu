@@ -58,6 +58,9 @@ struct md_sim {
     std::vector<SysDesc> sys;
     double mass[kMaxTypes], inv_mass[kMaxTypes];
     double skin = 0.3, rc_max = 0.0;
+    bool coul = false;                 // shifted-force Coulomb term on (Sec. 8)
+    double charge[kMaxTypes] = {};
+    double rcc = 0.0;                  // Coulomb cutoff rc_C
     int integrator = MD_NVE_LEAPFROG;
     double dt = 0.005, T0 = 1.0, tau = 0.2;
     int tp = 1, block = 128, reach = 2, tpb = 8;
@@ -234,7 +237,7 @@ int configure_layout(md_sim *s, bool realloc_cells) {
         int optin3 = 0;
         cudaDeviceGetAttribute(&optin3, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
         s->staged_smem = (size_t)s->rep_nmax * 16;
-        s->staged_ok = s->precision == MD_MIXED && s->cutoff == MD_SHIFTED_POTENTIAL &&
+        s->staged_ok = s->precision == MD_MIXED && s->cutoff == MD_SHIFTED_POTENTIAL && !s->coul &&
                        s->staged_smem + 8192 <= (size_t)optin3 &&
                        s->staged_smem <= 100 * 1024 &&
                        prepare_step_staged(s->tp, s->nt == 1, s->staged_smem) == cudaSuccess;
@@ -248,7 +251,7 @@ int configure_layout(md_sim *s, bool realloc_cells) {
     // resident CTAs per SM: shared memory (plus ~8 KB static) and 64 registers x threads
     s->rep_ctas = std::max(1, std::min(per_sm / (int)(s->rep_smem + 8192),
                                        65536 / (64 * s->rep_threads)));
-    s->rep_ok = s->precision == MD_MIXED && s->cutoff == MD_SHIFTED_POTENTIAL &&
+    s->rep_ok = s->precision == MD_MIXED && s->cutoff == MD_SHIFTED_POTENTIAL && !s->coul &&
                 s->rep_smem + 8192 <= (size_t)optin &&
                 (s->tpb == 8 || s->tpb == 32) &&
                 prepare_rep(s->tp, s->tpb, s->nt == 1, s->rep_smem) == cudaSuccess;
@@ -349,6 +352,7 @@ template <typename R> StepArgs<R> step_args(md_sim *s, int parity, int force_onl
     a.has_next = 0;
     a.need_filter = -1;
     a.cutoff = s->cutoff;
+    a.coulomb = s->coul ? 1 : 0;
     a.nolist = s->list_method == 2 ? 1 : 0;
     return a;
 }
@@ -648,6 +652,22 @@ void unpack_v4(const md_sim *s, const std::vector<unsigned char> &src, size_t k,
         std::memcpy(v, src.data() + k * 16, 16);
         out3[0] = v[0]; out3[1] = v[1]; out3[2] = v[2];
     }
+}
+
+// Interaction range of type pair p: the LJ cutoff, or the Coulomb cutoff if larger.
+double pair_range(const md_sim *s, int p) {
+    return s->coul ? std::max(s->params[p].rc, s->rcc) : s->params[p].rc;
+}
+
+// List thresholds (rc_p + s)^2 of every type pair, then the table upload.
+int upload_thresholds(md_sim *s) {
+    for (int p = 0; p < s->nt * s->nt; ++p) {
+        const double rc = pair_range(s, p), thr2 = (rc + s->skin) * (rc + s->skin);
+        s->tab[p].thr2d = thr2;
+        s->tab[p].thr2 = (float)thr2;
+    }
+    return cudaMemcpy(s->b.tab, s->tab.data(), sizeof(PairTab) * MD_MAX_PAIRS,
+                      cudaMemcpyHostToDevice) == cudaSuccess ? 0 : 1;
 }
 
 }  // namespace
@@ -1232,6 +1252,47 @@ int md_set_list_method(md_sim *s, int method) {
     return method == 2 ? MD_OK : request_rebuild_all(s);
 }
 
+int md_set_coulomb(md_sim *s, const double *charge, double rc_coulomb) {
+    if (!s) return MD_EINVAL;
+    const bool on = charge != nullptr && rc_coulomb > 0.0;
+    if (charge && !(rc_coulomb > 0.0 && std::isfinite(rc_coulomb))) return MD_EINVAL;
+    if (on)
+        for (int t = 0; t < s->nt; ++t)
+            if (!std::isfinite(charge[t])) return MD_EINVAL;
+    double rc_max = 0.0;
+    for (auto &p : s->params) rc_max = std::max(rc_max, p.rc);
+    if (on) rc_max = std::max(rc_max, rc_coulomb);
+    for (int r = 0; r < s->R; ++r)
+        if (!(s->L[r] > 2.0 * (rc_max + s->skin))) return MD_EINVAL;
+    if (s->sticky) return s->sticky;
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(s, MD_ECUDA);
+    destroy_graphs(s);
+    s->coul = on;
+    s->rcc = on ? rc_coulomb : 0.0;
+    s->rc_max = rc_max;
+    for (int t = 0; t < kMaxTypes; ++t) s->charge[t] = (on && t < s->nt) ? charge[t] : 0.0;
+    for (int a = 0; a < s->nt; ++a)
+        for (int c = 0; c < s->nt; ++c) {
+            PairTab &t = s->tab[a * s->nt + c];
+            const double qq = s->charge[a] * s->charge[c], rcc = s->rcc;
+            // an off term gets a zero range, so no pair ever passes r2 < qrc2
+            t.qrc2d = on ? rcc * rcc : 0.0;
+            t.qqd = qq;
+            t.qfd = on ? qq / (rcc * rcc) : 0.0;
+            t.qud = on ? 2.0 * qq / rcc : 0.0;
+            t.qrc2 = (float)t.qrc2d; t.qq = (float)t.qqd; t.qf = (float)t.qfd; t.qu = (float)t.qud;
+        }
+    if (upload_thresholds(s)) return fail(s, MD_ECUDA);
+    const int need = estimate_nmax(s);
+    if (need > s->nmax) {
+        s->nmax = need;
+        if (alloc_nbl(s)) return MD_ENOMEM;
+    }
+    int rc = configure_layout(s, true);   // cell edge and kernel paths follow the new range
+    if (rc) return rc == MD_ENOMEM ? MD_ENOMEM : fail(s, MD_ECUDA);
+    return request_rebuild_all(s);
+}
+
 int md_set_skin(md_sim *s, double skin) {
     if (!s || !(skin > 0.0) || !std::isfinite(skin)) return MD_EINVAL;
     if (s->sticky) return s->sticky;
@@ -1240,14 +1301,7 @@ int md_set_skin(md_sim *s, double skin) {
     if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(s, MD_ECUDA);
     destroy_graphs(s);
     s->skin = skin;
-    for (int p = 0; p < s->nt * s->nt; ++p) {
-        const double rc = s->params[p].rc, thr2 = (rc + skin) * (rc + skin);
-        s->tab[p].thr2d = thr2;
-        s->tab[p].thr2 = (float)thr2;
-    }
-    if (cudaMemcpy(s->b.tab, s->tab.data(), sizeof(PairTab) * MD_MAX_PAIRS,
-                   cudaMemcpyHostToDevice) != cudaSuccess)
-        return fail(s, MD_ECUDA);
+    if (upload_thresholds(s)) return fail(s, MD_ECUDA);
     const int need = estimate_nmax(s);
     if (need > s->nmax) {
         s->nmax = need;
@@ -1631,6 +1685,11 @@ std::string tune_key(md_sim *s) {
     for (auto &p : s->params) {
         const float q[3] = {(float)p.eps, (float)p.sigma, (float)p.rc};
         mix(q, sizeof(q));
+    }
+    mix(&s->cutoff, sizeof(int));
+    if (s->coul) {
+        mix(&s->rcc, sizeof(double));
+        mix(s->charge, sizeof(double) * s->nt);
     }
     char buf[512];
     std::snprintf(buf, sizeof(buf), "gpu=%s|R=%d|N=%d|nt=%d|prec=%d|skin=%.4g|integ=%d|dt=%.6g|T=%.4g|h=%016llx",

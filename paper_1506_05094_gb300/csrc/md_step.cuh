@@ -31,12 +31,13 @@ template <bool NC> __device__ __forceinline__ int ld_idx(const int *p) {
 
 // NC: the list may be read through the non-coherent read-only path (it was written by an
 // earlier kernel); false when the same kernel has just built it.
-template <typename R, int TP, bool SINGLE, typename Src, bool NC = true, bool SF = false>
+template <typename R, int TP, bool SINGLE, typename Src, bool NC = true, int SF = 0>
 __device__ __forceinline__ void force_sum(const StepArgs<R> &a, const Src &P4, int i,
                                           const typename V4T<R>::t &ri, int ti, const Frame<R> &F,
                                           int lt, const typename Coef4<R>::t *s_c0,
                                           const typename Coef4<R>::t *s_c1, R &fx, R &fy, R &fz,
-                                          R &u, R &w) {
+                                          R &u, R &w,
+                                          const typename Coef4<R>::t *s_cq = nullptr) {
     typedef typename V4T<R>::t V4;
     const typename Coef4<R>::t c1 = s_c0[0];
     const typename Coef4<R>::t c1b = s_c1[0];
@@ -56,33 +57,34 @@ __device__ __forceinline__ void force_sum(const StepArgs<R> &a, const Src &P4, i
             j0 = ld_idx<NC>(q); j1 = ld_idx<NC>(q + stride); j2 = ld_idx<NC>(q + 2 * stride);
             j3 = ld_idx<NC>(q + 3 * stride);
         }
-        interact<R, SINGLE, SF>(ri, ti, r0, F, a.ntypes, s_c0, s_c1, c1, c1b, fx, fy, fz, u, w);
-        interact<R, SINGLE, SF>(ri, ti, r1, F, a.ntypes, s_c0, s_c1, c1, c1b, fx, fy, fz, u, w);
-        interact<R, SINGLE, SF>(ri, ti, r2, F, a.ntypes, s_c0, s_c1, c1, c1b, fx, fy, fz, u, w);
-        interact<R, SINGLE, SF>(ri, ti, r3, F, a.ntypes, s_c0, s_c1, c1, c1b, fx, fy, fz, u, w);
+        interact<R, SINGLE, SF>(ri, ti, r0, F, a.ntypes, s_c0, s_c1, c1, c1b, fx, fy, fz, u, w, s_cq);
+        interact<R, SINGLE, SF>(ri, ti, r1, F, a.ntypes, s_c0, s_c1, c1, c1b, fx, fy, fz, u, w, s_cq);
+        interact<R, SINGLE, SF>(ri, ti, r2, F, a.ntypes, s_c0, s_c1, c1, c1b, fx, fy, fz, u, w, s_cq);
+        interact<R, SINGLE, SF>(ri, ti, r3, F, a.ntypes, s_c0, s_c1, c1, c1b, fx, fy, fz, u, w, s_cq);
     }
     for (; k < nn; k += TP) {
         const int j = ld_idx<NC>(q);
         q += stride;
-        interact<R, SINGLE, SF>(ri, ti, P4(j), F, a.ntypes, s_c0, s_c1, c1, c1b, fx, fy, fz, u, w);
+        interact<R, SINGLE, SF>(ri, ti, P4(j), F, a.ntypes, s_c0, s_c1, c1, c1b, fx, fy, fz, u, w, s_cq);
     }
 }
 
 // No list: every other particle of the replica, TP lanes per particle (the mode the paper uses
 // for very small systems, Appendix).
-template <typename R, int TP, bool SINGLE, bool SF, typename Src>
+template <typename R, int TP, bool SINGLE, int SF, typename Src>
 __device__ __forceinline__ void force_all(const StepArgs<R> &a, const Src &P4, const SysDesc &S,
                                           int i, const typename V4T<R>::t &ri, int ti,
                                           const Frame<R> &F, int lt,
                                           const typename Coef4<R>::t *s_c0,
                                           const typename Coef4<R>::t *s_c1, R &fx, R &fy, R &fz,
-                                          R &u, R &w) {
+                                          R &u, R &w,
+                                          const typename Coef4<R>::t *s_cq = nullptr) {
     const typename Coef4<R>::t c1 = s_c0[0];
     const typename Coef4<R>::t c1b = s_c1[0];
     for (int j = S.off + lt; j < S.off + S.n; j += TP)
         if (j != i)
             interact<R, SINGLE, SF>(ri, ti, P4(j), F, a.ntypes, s_c0, s_c1, c1, c1b, fx, fy, fz,
-                                    u, w);
+                                    u, w, s_cq);
 }
 
 // Merge the TP partial sums of each particle (replaces the serial shared-memory sum of Fig. 2).
@@ -282,7 +284,8 @@ template <typename R> __device__ __forceinline__ void close_step(const StepArgs<
 // STAGE: the CTA first copies its replica's positions into shared memory and gathers the
 // neighbour positions from there (replicas that fit; the copy is repeated by every tile of the
 // replica and is served from L2).
-template <typename R, int TP, bool SINGLE, bool STAGE = false, bool SF = false>
+// SF: potential kind of interact() (bit 0 LJ shifted force, bit 1 Coulomb).
+template <typename R, int TP, bool SINGLE, bool STAGE = false, int SF = 0>
 __global__ void __launch_bounds__(1024) k_step(const StepArgs<R> a) {
     typedef typename V4T<R>::t V4;
     typedef typename Coef4<R>::t C4;
@@ -291,6 +294,7 @@ __global__ void __launch_bounds__(1024) k_step(const StepArgs<R> a) {
 
     __shared__ C4 s_c0[MD_MAX_PAIRS];
     __shared__ C2 s_c1[MD_MAX_PAIRS];
+    __shared__ C4 s_cq[(SF & 2) ? MD_MAX_PAIRS : 1];
     __shared__ R s_im[MD_MAX_TYPES], s_m[MD_MAX_TYPES];
     __shared__ double s_tmp[32][MD_NRED];
     __shared__ double s_red[MD_NRED];
@@ -305,6 +309,9 @@ __global__ void __launch_bounds__(1024) k_step(const StepArgs<R> a) {
     if (a.need_filter >= 0 && ((a.need_in[r] != 0) != (a.need_filter != 0))) return;
     const SysDesc S = a.sys[r];
     load_tables(a, s_c0, s_c1, s_im, s_m);
+    if (SF & 2)
+        for (int p = threadIdx.x; p < a.ntypes * a.ntypes; p += blockDim.x)
+            s_cq[p] = coef2_of<R>(a.tab[p]);
     if (threadIdx.x == 0) {
         // one uniform decision per block: a halt or an unrecovered list overflow stops the step
         s_skip = *(volatile int *)&a.ctrl->halt | *(volatile int *)&a.ctrl->overflow;
@@ -337,14 +344,15 @@ __global__ void __launch_bounds__(1024) k_step(const StepArgs<R> a) {
         if (STAGE) {
             SharedPos<R> src{s_pos, S.off};
             force_sum<R, TP, SINGLE, SharedPos<R>, true, SF>(a, src, i, ri, ti, F, lt, s_c0, s_c1,
-                                                             fx, fy, fz, u, w);
+                                                             fx, fy, fz, u, w, s_cq);
         } else if (a.nolist) {
             GlobalPos<R> src{a.pos_in};
-            force_all<R, TP, SINGLE, SF>(a, src, S, i, ri, ti, F, lt, s_c0, s_c1, fx, fy, fz, u, w);
+            force_all<R, TP, SINGLE, SF>(a, src, S, i, ri, ti, F, lt, s_c0, s_c1, fx, fy, fz, u, w,
+                                         s_cq);
         } else {
             GlobalPos<R> src{a.pos_in};
             force_sum<R, TP, SINGLE, GlobalPos<R>, true, SF>(a, src, i, ri, ti, F, lt, s_c0, s_c1,
-                                                             fx, fy, fz, u, w);
+                                                             fx, fy, fz, u, w, s_cq);
         }
     }
     merge_lanes<R, TP>(fx, fy, fz, u, w);

@@ -26,7 +26,7 @@ LOG_COLS = ("step", "U", "W", "K_minus", "K_plus", "xi", "xi_int", "H", "px", "p
 SYMBOLS = ("md_create", "md_set_integrator", "md_set_state", "md_set_stream", "md_step",
            "md_sync", "md_get_state", "md_get_energies", "md_get_forces", "md_get_neighbors",
            "md_set_tuning", "md_get_tuning", "md_set_skin", "md_get_skin", "md_set_list_capacity",
-           "md_set_path", "md_set_list_method",
+           "md_set_path", "md_set_list_method", "md_set_coulomb",
            "md_set_graph_block", "md_autotune",
            "md_get_stats", "md_profile", "md_set_log", "md_get_log", "md_checkpoint_size",
            "md_save_checkpoint", "md_load_checkpoint", "md_destroy", "md_strerror",
@@ -98,6 +98,7 @@ def lib():
         "md_set_list_capacity": [p, i],
         "md_set_path": [p, i],
         "md_set_list_method": [p, i],
+        "md_set_coulomb": [p, pd, d],
         "md_set_graph_block": [p, i],
         "md_autotune": [p, C.c_char_p, i, i],
         "md_set_skin": [p, d],
@@ -186,8 +187,11 @@ class Sim:
             boxes = [s.L for s in states_or_sizes]
         else:
             sizes = states_or_sizes
-        return cls(sizes, boxes, model.eps, model.sigma, model.rc, model.mass, skin, precision,
-                   stream, cutoff)
+        sim = cls(sizes, boxes, model.eps, model.sigma, model.rc, model.mass, skin, precision,
+                  stream, cutoff)
+        if getattr(model, "coulomb", False):
+            sim.set_coulomb(model.charge, model.rc_coulomb)
+        return sim
 
     # ---- lifecycle
     def close(self):
@@ -253,6 +257,15 @@ class Sim:
         _ck(lib().md_autotune(self._h, cp, int(steps_per_trial), 1 if tune_skin else 0),
             "md_autotune")
         return self.get_tuning()
+
+    def set_coulomb(self, charge, rc_coulomb: float):
+        """Shifted-force Coulomb term: per-type charges (reduced units) cut at rc_coulomb;
+        charge None switches it off."""
+        if charge is None:
+            _ck(lib().md_set_coulomb(self._h, None, 0.0), "md_set_coulomb")
+            return
+        q = np.ascontiguousarray(charge, dtype=np.float64)
+        _ck(lib().md_set_coulomb(self._h, _dptr(q), float(rc_coulomb)), "md_set_coulomb")
 
     def set_skin(self, skin: float):
         _ck(lib().md_set_skin(self._h, float(skin)), "md_set_skin")
