@@ -9,8 +9,9 @@ The ensemble's working set (neighbour list ~0.45 GB) exceeds the 129 MB L2, so n
 needed between timed steps.
 
 Also reported in the same line: the same replicas run one after another with plain kernel
-launches (the baseline of the batched form), the single-system workloads (KA N = 8000 NVT and
-LJ N = 131072 NVE, L2-flushed between individually timed steps), the dominant kernel's roofline
+launches (the baseline of the batched form), the single-system workloads (KA N = 8000 NVT,
+LJ N = 131072 NVE and the N = 20000 molten salt with shifted-force Coulomb, L2-flushed between
+individually timed steps), the dominant kernel's roofline
 position, an end-to-end number through the C ABI with host buffers, and the FP64 CPU oracle timed
 on a bounded sample (cpu_baseline).
 
@@ -47,7 +48,14 @@ WORKLOAD_NAMES = {
     "ka8000": "KA N=8000 rho=1.2, NVT T=0.44 dt=0.0025 skin=0.3",
     "lj131072": "LJ N=131072 fcc rho=0.8442, NVE T=0.72 dt=0.005 skin=0.3",
     "lj1000": "LJ N=1000 fcc rho=0.8442, NVE T=0.72 dt=0.005 skin=0.3",
+    "salt2000": "molten salt N=2000 (charged LJ, q=+-1, Coulomb SF rc=6.0) rho=0.3677, "
+                "NVT T=2 dt=0.004 skin=0.3",
+    "salt20000": "molten salt N=20000 (charged LJ, q=+-1, Coulomb SF rc=6.0) rho=0.3677, "
+                 "NVT T=2 dt=0.004 skin=0.3",
+    "salt100000": "molten salt N=100000 (charged LJ, q=+-1, Coulomb SF rc=6.0) rho=0.3677, "
+                  "NVT T=2 dt=0.004 skin=0.3",
 }
+L2_BYTES = 129e6
 UNIT = "particle-steps/s"
 GRAPH_BLOCK = 100
 
@@ -174,6 +182,43 @@ def step_kernel_bytes(n_total: int, entries: int, precision: str) -> float:
     return float(per * n_total + 4 * entries)
 
 
+# FP32 arithmetic per unit of work of the fused step kernel (add/sub/mul 1, FMA 2, MUFU 1):
+#   every list entry (pair test): minimum image 3 x 4, dist^2 5, compare 1          = 18
+#   every LJ pair inside rc_ab: 1/r^2, r^-6, force scalar, energy, 3 force FMAs, virial
+#                               = 20 (shifted potential), 27 (shifted force)
+#   every Coulomb pair inside rc_C: 1/r, force scalar, energy, 3 force FMAs, virial    = 18
+#   every particle: integrate + skin check                                             = 30
+FLOP_TEST, FLOP_LJ_SP, FLOP_LJ_SF, FLOP_COUL, FLOP_PARTICLE = 18, 20, 27, 18, 30
+FP32_LANES_PER_SM = 128
+
+
+def step_kernel_flops(wl, entries: int, cutoff: str = "sp") -> float:
+    """Algorithmic FP32 flops of one fused step-kernel launch over the workload.
+
+    The number of pairs inside each cutoff is taken from the listed pairs at uniform density:
+    a pair of types (a, b) listed within rc_list + s is inside rc with probability
+    (rc / (rc_list + s))^3, averaged over the type fractions of the workload's states."""
+    m = wl.model
+    nt = m.n_types
+    counts = np.zeros(nt)
+    for st in wl.states:
+        counts += np.bincount(st.types, minlength=nt)[:nt]
+    x = counts / counts.sum()
+    rl = np.asarray(m.rc_list, dtype=np.float64) + wl.skin
+    w = np.outer(x, x) * rl ** 3                      # listed pairs per type pair (relative)
+    w = w / w.sum()
+    f_lj = float((w * (np.asarray(m.rc) / rl) ** 3).sum())
+    f_c = float((w * (m.rc_coulomb / rl) ** 3).sum()) if m.coulomb else 0.0
+    per_lj = FLOP_LJ_SF if cutoff == "sf" else FLOP_LJ_SP
+    return float(entries * (FLOP_TEST + f_lj * per_lj + f_c * FLOP_COUL)
+                 + FLOP_PARTICLE * wl.n_total)
+
+
+def fp32_peak_tflops(sm_mhz: float, nsm: int = 152) -> float:
+    """FP32 pipe peak from unit counts and the SM clock: SMs x 128 lanes x 2 flop (FMA)."""
+    return nsm * FP32_LANES_PER_SM * 2.0 * sm_mhz * 1e6 / 1e12
+
+
 def pick_block(steps: int) -> int:
     """Graph block for a timed run of `steps`: 100 when it divides, else the largest even
     divisor up to 200 (an odd count leaves one plain step)."""
@@ -205,6 +250,27 @@ def l2_flush_buffer():
     return torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
 
+def time_steps_flushed(sim, stream_obj, steps: int):
+    """Sum of per-step durations (CUDA events on the sim's stream), the L2 flushed by a 256 MB
+    write before every step; the steps run as plain launches."""
+    import torch
+
+    flush = l2_flush_buffer()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    tot = 0.0
+    for _ in range(steps):
+        with torch.cuda.stream(stream_obj):
+            flush.fill_(1.0)
+        e0.record(stream_obj)
+        sim.step(1)
+        e1.record(stream_obj)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+    del flush
+    return tot
+
+
 def time_single_system(name, stream_obj, steps, warmup):
     """Single system, each step timed alone with CUDA events and L2 flushed in between."""
     import torch
@@ -214,18 +280,7 @@ def time_single_system(name, stream_obj, steps, warmup):
     sim.autotune(os.path.join(ROOT, "paper_1506_05094_gb300", "tune_cache.txt"), 50)
     sim.set_graph_block(0)
     sim.step(max(warmup, 3))
-    flush = l2_flush_buffer()
-    tot = 0.0
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    for _ in range(steps):
-        with torch.cuda.stream(stream_obj):
-            flush.fill_(1.0)
-        e0.record(stream_obj)
-        sim.step(1)
-        e1.record(stream_obj)
-        e1.synchronize()
-        tot += e0.elapsed_time(e1)
+    tot = time_steps_flushed(sim, stream_obj, steps)
     # back-to-back graph replay of the same system (L2 stays warm: working set stated)
     sim.set_graph_block(GRAPH_BLOCK)
     sim.step(GRAPH_BLOCK)
@@ -237,20 +292,22 @@ def time_single_system(name, stream_obj, steps, warmup):
            "ms_per_step_graph_l2_warm": ms_graph, "value_graph_l2_warm": n / (ms_graph / 1e3),
            "tuning": list(sim.get_tuning()), "rebuild_passes": st["rebuild_passes"]}
     sim.close()
-    del flush
     return out
 
 
 def cpu_baseline(wl, max_seconds=15.0):
-    """The FP64 oracle (O(N^2) plain definition, OpenMP) on a bounded sample of the workload."""
+    """The FP64 oracle on a bounded sample of the workload: the plain O(N^2) definition for
+    replicas and systems up to 20000 particles, its linked-cell mode (equal to it, pinned in the
+    oracle tests) above; OpenMP over particles."""
     import oracle
 
     threads = oracle.threads()
     done_ps, spent = 0, 0.0
     picked = []
+    cells = max(s.n for s in wl.states) > 20000
     for s in wl.states:
         run = oracle.Run(s.pos, s.vel, s.types, s.L, wl.model, wl.integrator, wl.dt, T=wl.T,
-                         tau=wl.tau)
+                         tau=wl.tau, cells=cells)
         t0 = time.perf_counter()
         run.run(2)
         dt = time.perf_counter() - t0
@@ -259,41 +316,57 @@ def cpu_baseline(wl, max_seconds=15.0):
         picked.append(s.n)
         if spent >= max_seconds:
             break
+    kind = "linked cells" if cells else "O(N^2)"
     return {"value": done_ps / spent, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{len(picked)} replicas (N={picked[0]}..), 2 NVT steps each, O(N^2) FP64",
+            "sample": f"{len(picked)} of {len(wl.states)} systems (N={picked[0]}..), 2 "
+                      f"{wl.integrator.upper()} steps each, {kind} FP64",
             "seconds": spent}
 
 
 # ------------------------------------------------------------------------------ reference arm
 
-def run_reference(args):
+def run_reference(args, max_seconds=120.0):
+    """The FP64 oracle as it stands on the host cores, on the same workload: the ensemble's
+    first 4 replicas (O(N^2)), or the single system (O(N^2) up to 20000 particles, linked cells
+    above); timing stops after max_seconds of steps (the sample actually run is stated)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     import oracle
 
-    wl = synth.workload("ka_ensemble512", replicas=4)
+    if args.workload == "ka_ensemble512":
+        wl = synth.workload("ka_ensemble512", replicas=4)
+        what = "KA ensemble: first 4 of the 512 replicas (N=%s), NVT T=0.8" % [s.n for s in wl.states]
+    else:
+        wl = synth.workload(args.workload)
+        what = WORKLOAD_NAMES[args.workload]
+    cells = max(s.n for s in wl.states) > 20000
     threads = oracle.threads()
     runs = [oracle.Run(s.pos, s.vel, s.types, s.L, wl.model, wl.integrator, wl.dt, T=wl.T,
-                       tau=wl.tau) for s in wl.states]
+                       tau=wl.tau, cells=cells) for s in wl.states]
     n_sample = sum(s.n for s in wl.states)
     for _ in range(args.warmup):
         for r in runs:
             r.run(1)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    done = 0
+    while done < args.steps:
         for r in runs:
             r.run(1)
+        done += 1
+        if time.perf_counter() - t0 > max_seconds:
+            break
     sec = time.perf_counter() - t0
-    value = n_sample * args.steps / sec
+    value = n_sample * done / sec
+    kind = "linked cells" if cells else "O(N^2)"
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / done,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": "KA ensemble: first 4 of the 512 replicas (N=%s), NVT T=0.8"
-                                   % [s.n for s in wl.states], "sample_particles": n_sample},
+            "config": {"workload": what, "sample_particles": n_sample, "steps_run": done},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": f"4 replicas, {args.steps} steps, O(N^2) FP64"},
+                             "sample": f"{len(runs)} system(s), {done} of {args.steps} steps "
+                                       f"(stops after {max_seconds:.0f} s), {kind} FP64"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -312,7 +385,7 @@ def main():
     ap.add_argument("--replicas", type=int, default=None, help="trim the ensemble (profiling)")
     ap.add_argument("--tuning", default=None, help="tp,block,reach[,lanes]: skip the autotuner")
     ap.add_argument("--workload", default="ka_ensemble512",
-                    choices=["ka_ensemble512", "ka8000", "lj131072", "lj1000"],
+                    choices=sorted(WORKLOAD_NAMES),
                     help="timed workload (default: the batched ensemble)")
     ap.add_argument("--path", default=None, choices=["grid", "replica", "staged"],
                     help="force a kernel path (default: the autotuner's choice)")
@@ -362,6 +435,10 @@ def main():
     sim.step(gb)                     # capture the graph (setup, untimed)
     sim.step(args.warmup)            # warm-up steps, untimed
     st0 = sim.stats()
+    # working set of a step: list indices + ~100 B of per-particle state; below the L2 size the
+    # steps are timed one by one with the L2 flushed in between
+    ws_bytes = 4.0 * st0["neighbor_entries"] + 100.0 * n_total
+    flushed = ws_bytes < L2_BYTES
 
     def barrier():
         if world > 1:
@@ -370,7 +447,8 @@ def main():
 
     barrier()
     with Clocks(local) as ck:
-        ms = time_steps(sim, stream, args.steps)
+        ms = (time_steps_flushed(sim, stream, args.steps) if flushed
+              else time_steps(sim, stream, args.steps))
     barrier()
     clocks = ck.summary()
     st1 = sim.stats()
@@ -384,9 +462,12 @@ def main():
     nk = st1["rebuild_kernels"]
     if path == "replica":   # one replica-resident launch per step, rebuilds inside it
         gpu_launches = args.steps
-    else:   # step kernels (two per graph step when split), arm per graph, nk per rebuild pass
-        sk = st1["step_kernels"]
-        gpu_launches = sk * (args.steps - rem) + rem + n_graphs + nk * passes + nk * rem
+    elif flushed:           # plain launches: the rebuild kernels and one step kernel per step
+        gpu_launches = args.steps * (nk + 1)
+    elif st1["step_kernels"] == 2:   # split graph steps: two step kernels, the rebuild kernels
+        gpu_launches = 2 * (args.steps - rem) + rem + nk * (args.steps - rem) + nk * rem
+    else:   # IF-node graphs: one step kernel per step, an arm kernel per graph, nk per pass
+        gpu_launches = (args.steps - rem) + rem + n_graphs + nk * passes + nk * rem
 
     # dominant kernel: fused step kernel, plain launches with CUDA events on the sim's stream
     prof = sim.profile(50)
@@ -395,14 +476,34 @@ def main():
     achieved = bytes_launch / (prof["step_kernel_ms"] * 1e-3) / 1e9
     tr = traffic_per_particle()
     traffic = None if tr is None else tr["dram_bytes_per_particle"] * n_total
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                "kernel": "k_step (force+integrate+check+reductions)",
-                "step_kernel_ms": prof["step_kernel_ms"],
-                "algorithmic_bytes_per_launch": bytes_launch,
-                "peak_kind": f"{peak_kind} hbm_gbs (burst copy)",
-                "rebuild_pass_ms": prof["rebuild_ms"],
-                "rebuild_passes_per_step": prof["rebuild_fraction"]}
+    # FP32 pipe bound at the clock sampled during the timed region (max clock if none)
+    flops_launch = step_kernel_flops(wl, prof["neighbor_entries"])
+    sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    p_fp32 = fp32_peak_tflops(sm_mhz, torch.cuda.get_device_properties(local).multi_processor_count)
+    t_hbm = bytes_launch / (peaks["hbm_gbs"] * 1e9)
+    t_alu = flops_launch / (p_fp32 * 1e12)
+    alu_achieved = flops_launch / (prof["step_kernel_ms"] * 1e-3) / 1e12
+    alu = {"achieved": alu_achieved, "peak": p_fp32, "unit": "TFLOP/s",
+           "frac": alu_achieved / p_fp32, "flops_per_launch": flops_launch,
+           "peak_kind": "derived: SMs x 128 FP32 lanes x 2 flop x median SM clock %.0f MHz"
+                        % sm_mhz}
+    if t_alu > t_hbm:
+        roofline = {"bound": "alu", "achieved": alu_achieved, "peak": p_fp32, "unit": "TFLOP/s",
+                    "frac": alu_achieved / p_fp32, "traffic": traffic,
+                    "peak_kind": alu["peak_kind"],
+                    "hbm": {"achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                            "frac": achieved / peaks["hbm_gbs"]}}
+    else:
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                    "peak_kind": f"{peak_kind} hbm_gbs (burst copy)", "alu": alu}
+    roofline.update({"kernel": "k_step (force+integrate+check+reductions)",
+                     "step_kernel_ms": prof["step_kernel_ms"],
+                     "algorithmic_bytes_per_launch": bytes_launch,
+                     "t_roof_ms": max(t_hbm, t_alu) * 1e3,
+                     "roof_over_measured": max(t_hbm, t_alu) * 1e3 / prof["step_kernel_ms"],
+                     "rebuild_pass_ms": prof["rebuild_ms"],
+                     "rebuild_passes_per_step": prof["rebuild_fraction"]})
 
     extras = {}
     if rank == 0 and not args.no_extras:
@@ -449,8 +550,9 @@ def main():
                                                "steps": seq_steps,
                                                "batched_over_sequential": value / world / seq_value}
         # single systems
-        extras["single_system"] = [time_single_system("ka8000", stream, 200, args.warmup),
-                                   time_single_system("lj131072", stream, 200, args.warmup)]
+        extras["single_system"] = [time_single_system(w, stream, 200, args.warmup)
+                                   for w in ("ka8000", "lj131072", "salt20000")
+                                   if w != args.workload]
         extras["cpu_baseline"] = cpu_baseline(wl)
 
     if rank == 0:
@@ -462,9 +564,14 @@ def main():
                            "particles_per_gpu": n_total, "replicas": len(wl.states),
                            "graph_block": gb, "tuning_tp_block_reach_lanes": list(tuning),
                            "kernel_path": path,
+                           "list_method": ["cells", "n2", "none"][st1["list_method"]],
+                           "rebuild_slots_K": st1["rebuild_batch"],
                            "precision": "FP32 pair math, FP64 positions and reductions",
-                           "l2": "no flush: neighbour list %.2f GB > 129 MB L2"
-                                 % (4.0 * st1["neighbor_entries"] / 1e9),
+                           "l2": ("flushed: 256 MB written before every timed step "
+                                  "(working set %.1f MB < 129 MB L2; plain launches)"
+                                  % (ws_bytes / 1e6)) if flushed else
+                                 ("no flush: working set %.2f GB (neighbour list) > 129 MB L2"
+                                  % (ws_bytes / 1e9)),
                            "parallelism": f"replicas x{world}"},
                 "clocks": clocks, "gpu_launches": gpu_launches, "roofline": roofline}
         line.update(extras)

@@ -94,6 +94,7 @@ typedef struct {
     int build_lanes;            /* lanes per particle in the list build */
     int path;                   /* 1 grid, 2 replica-resident, 3 grid with staged positions */
     int list_method;            /* 0 sorted cells, 1 O(N^2) scan, 2 no list */
+    int rebuild_batch;          /* K of md_set_rebuild_batch */
     int rebuild_kernels;        /* kernels launched per rebuild pass on the grid path */
     int step_kernels;           /* step kernels per graph step (2: split around the rebuild) */
     int graph_block;            /* steps per captured CUDA graph (0 = plain launches) */
@@ -180,9 +181,9 @@ int md_set_list_capacity(md_sim *sim, int n_max);
  * kernels behind a CUDA-graph IF node), 2 = replica-resident kernel (persistent CTAs that each
  * run a whole step of one replica at a time in shared memory, rebuild included), 3 = grid kernels
  * with each tile's replica positions staged in shared memory for the neighbour gathers.  2 and 3
- * are mixed precision only and need replicas that fit in shared memory.  0 = automatic (2 when it
- * applies and there are at least 32 replicas, else 1).  All paths give the same results bit for
- * bit.  MD_EINVAL if the requested path does not apply. */
+ * are mixed precision only and need replicas that fit in shared memory.  0 = automatic (1; the
+ * autotuner times the others).  All paths give the same results bit for bit.  MD_EINVAL if the
+ * requested path does not apply. */
 enum { MD_PATH_AUTO = 0, MD_PATH_GRID = 1, MD_PATH_REPLICA = 2, MD_PATH_STAGED = 3 };
 int md_set_path(md_sim *sim, int path);
 
@@ -209,13 +210,25 @@ int md_set_list_method(md_sim *sim, int method);
  * on the grid kernel path (paths 2 and 3 are not used while it is on). */
 int md_set_coulomb(md_sim *sim, const double *charge, double rc_coulomb);
 
+/* Rebuild slots for batches of replicas (the paper runs one system and has no counterpart; its
+ * rule, a rebuild once some particle has moved more than s/2, Sec. 6, is kept).  K = 1 (default):
+ * a replica rebuilds exactly when that rule fires.  K > 1: in addition, at every K-th step a
+ * replica whose largest displacement since its build, grown by 1.5 x its largest one-step
+ * displacement per step, would pass s/2 within K - 1 more steps rebuilds now, so that rebuilds
+ * gather on the slot steps and one rebuild pass serves many replicas; the other steps usually
+ * rebuild nothing and skip the pass.  The list is valid either way (the s/2 rule still fires
+ * on any step); only the rebuild times, hence the list order and FP32 summation order, change.
+ * 1 <= K <= 64, MD_EINVAL otherwise. */
+int md_set_rebuild_batch(md_sim *sim, int k);
+
 /* List skin s (Sec. 4): pairs within rc + s are listed and the list is rebuilt when a particle
  * has moved more than s/2.  Changes only the work done, never the physics.  Needs
  * L > 2 (rc_max + s) for every replica; forces a rebuild of every replica. */
 int md_set_skin(md_sim *sim, double skin);
 int md_get_skin(md_sim *sim, double *skin);
 
-/* Parameter search of the Appendix, over the kernel path, tp, block, reach and build_lanes (and
+/* Parameter search of the Appendix, over the kernel path, the list method, the rebuild slots K
+ * (batches of 8 or more replicas), tp, block, reach and build_lanes (and
  * the skin when flags has MD_TUNE_SKIN: 20% then 10% steps until the time stops falling): short
  * timed runs from the
  * current state (restored after every trial), single-minimum line searches with the break rules

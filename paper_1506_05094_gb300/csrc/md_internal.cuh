@@ -122,6 +122,9 @@ template <typename R> struct StepArgs {
     double T0;
     double inv_tau2;
     R half_skin2;             // (s/2)^2
+    float half_skin;          // s/2
+    int rebuild_batch;        // K: rebuild slots every K steps (1: rebuild exactly when needed)
+    unsigned *disp;           // per replica: max |r - r_build|^2 and max one-step |dr|^2 (float bits)
     int force_only;           // 1: write f_out / w_out, no integration and no bookkeeping
     V4 *f_out;                // fx, fy, fz, u_i
     R *w_out;

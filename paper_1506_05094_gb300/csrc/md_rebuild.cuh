@@ -239,22 +239,55 @@ __device__ __forceinline__ int build_one(const SysDesc &S, const KeySrc &K, cons
     const int c = cell_index(ki, S);
     const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
     const bool full = (span == nc);
-    int xa0, xa1, xb0 = 0, xb1 = -1;   // x range of every row as one or two cell ranges
-    if (full) { xa0 = 0; xa1 = nc - 1; }
-    else {
-        const int x0 = cx - reach, x1 = cx + reach;
-        if (x0 < 0) { xa0 = x0 + nc; xa1 = nc - 1; xb0 = 0; xb1 = x1; }
-        else if (x1 >= nc) { xa0 = x0; xa1 = nc - 1; xb0 = 0; xb1 = x1 - nc; }
-        else { xa0 = x0; xa1 = x1; }
+    // Per-particle clipping of the stencil (the search volume of Sec. 7 is a cube of cells around
+    // the particle's cell; only cells that reach within rc + s of the particle itself can hold a
+    // neighbour).  In cell units the particle sits at fraction f of its cell along each axis; a
+    // cell d cells away is at least max(0, d - f) (d > 0) or f + |d| - 1 (d < 0) away along that
+    // axis.  Rows whose (y, z) gap already exceeds the particle's largest threshold are skipped
+    // and every row's x extent is cut to the cells within reach.  The bound carries a slack
+    // (1e-3 cell, 0.1 % of the threshold) far above FP32 rounding, so no accepted pair is ever
+    // dropped; the cells that remain are visited in the same order, so the list is unchanged.
+    float fxc = 0.f, fyc = 0.f, fzc = 0.f, lim2 = 0.f;
+    if (!full) {
+        const float cs = S.cell_scale;
+        fxc = __fmul_rn((float)ki.x, cs) - (float)cx;
+        fyc = __fmul_rn((float)ki.y, cs) - (float)cy;
+        fzc = __fmul_rn((float)ki.z, cs) - (float)cz;
+        float thr = 0.f;
+        for (int t = 0; t < ntypes; ++t) thr = fmaxf(thr, (float)s_thr[ti * ntypes + t]);
+        lim2 = thr * cs * cs * 1.001f + 1e-3f;
     }
-    // range q of the stencil: row q/2 in (z, y) order, part q%2 of its x extent
+    auto gap = [](int d, float f) -> float {
+        const float g = d > 0 ? (float)d - f : (d < 0 ? f - (float)d - 1.f : 0.f);
+        return fmaxf(g - 1e-3f, 0.f);
+    };
+    // range q of the stencil: row q/2 in (z, y) order, part q%2 of its x extent (two parts when
+    // the row wraps around the box)
     auto range = [&](int q) -> int2 {
         const int rowi = q >> 1, part = q & 1;
         const int oz = rowi / span, oy = rowi % span;
+        int lo, hi;
+        if (full) {
+            if (part) return make_int2(0, 0);
+            lo = 0;
+            hi = nc - 1;
+        } else {
+            const float gy = gap(oy - reach, fyc), gz = gap(oz - reach, fzc);
+            const float rem = lim2 - gy * gy - gz * gz;
+            if (rem <= 0.f) return make_int2(0, 0);
+            const float w = sqrtf(rem);
+            const int x0 = cx - min(reach, (int)(w - fxc + 1.001f));
+            const int x1 = cx + min(reach, (int)(w + fxc + 0.001f));
+            int a0, a1, b0 = 0, b1 = -1;
+            if (x0 < 0) { a0 = x0 + nc; a1 = nc - 1; b0 = 0; b1 = x1; }
+            else if (x1 >= nc) { a0 = x0; a1 = nc - 1; b0 = 0; b1 = x1 - nc; }
+            else { a0 = x0; a1 = x1; }
+            lo = part ? b0 : a0;
+            hi = part ? b1 : a1;
+        }
         const int zz = full ? oz : (cz - reach + oz + nc) % nc;
         const int yy = full ? oy : (cy - reach + oy + nc) % nc;
         const int row = (zz * nc + yy) * nc;
-        const int lo = part ? xb0 : xa0, hi = part ? xb1 : xa1;
         return (hi < lo) ? make_int2(0, 0) : make_int2(CS(row + lo), CS(row + hi + 1));
     };
     const int nr = span * span * 2;

@@ -114,6 +114,7 @@ __global__ void __launch_bounds__(1024) k_rep(const StepArgs<R> a, const Rebuild
     __shared__ double s_xi;
     __shared__ R s_A, s_B;
     __shared__ int s_job, s_skip, s_ovf;
+    __shared__ unsigned s_disp[2];   // replica maxima of the displacement measures
     __shared__ SysDesc S;   // the replica being processed (shared: keeps registers free)
 
     load_tables(a, s_c0, s_c1, s_im, s_m);
@@ -238,6 +239,8 @@ __global__ void __launch_bounds__(1024) k_rep(const StepArgs<R> a, const Rebuild
         // ---- forces over the list (shared-memory gathers), integration, tile partials ----
         const bool direct = s_ovf != 0;
         int moved_any = 0;
+        if (threadIdx.x < 2) s_disp[threadIdx.x] = 0u;
+        __syncthreads();
         for (int t0 = 0; t0 < S.ntiles; t0 += tpb_tiles) {
             const int t = t0 + tsub;
             const int li = t * P + lp;
@@ -265,10 +268,12 @@ __global__ void __launch_bounds__(1024) k_rep(const StepArgs<R> a, const Rebuild
             w *= R(1.0 / 6.0);
             R ke = 0, px = 0, py = 0, pz = 0;
             bool moved = false;
+            float d2 = 0.f, st2 = 0.f;
             if (leader)
                 moved = integrate_one(a, S, i, ri, fx, fy, fz, s_im[ti], s_m[ti], s_A, s_B, ke,
-                                      px, py, pz);
+                                      px, py, pz, d2, st2);
             moved_any |= (int)moved;
+            if (a.rebuild_batch > 1) disp_max_warp(s_disp, d2, st2);
             R vals[MD_NRED] = {u * R(leader), w * R(leader), ke, px, py, pz};
             // partials of tiles past the replica's last one are written to spare rows and ignored
             tile_partial(vals, s_tmp, s_part + (long long)t0 * MD_NRED, TT >> 5);
@@ -278,7 +283,7 @@ __global__ void __launch_bounds__(1024) k_rep(const StepArgs<R> a, const Rebuild
         // an overflowed list stays flagged: every step rebuilds and evaluates list-free until the
         // host has grown the capacity
         replica_finish(a, r, S, s_part, s_xi, (moved_any || direct) ? 1 : 0, s_tmp, s_red, false,
-                       TT);
+                       TT, __uint_as_float(s_disp[0]), __uint_as_float(s_disp[1]));
         __syncthreads();
     }
     // last CTA closes the step

@@ -39,6 +39,7 @@ struct Buffers {
     Thermo *th = nullptr;
     Ctrl *ctrl = nullptr;
     int *moved = nullptr, *need = nullptr;
+    unsigned *disp = nullptr;   // 2 per replica: displacement maxima of the current step
     unsigned *ticket = nullptr;
     double *partial = nullptr;
     int *tile_rep = nullptr;
@@ -66,6 +67,7 @@ struct md_sim {
     int tp = 1, block = 128, reach = 2, tpb = 8;
     int path = 0;            // 0 auto, 1 grid, 2 replica-resident
     int list_method = 0;     // 0 sorted cells, 1 O(N^2) scan, 2 no list
+    int rebuild_batch = 1;   // K: rebuild slots every K steps (1: rebuild exactly when needed)
     bool rep_ok = false;     // replica-resident kernel usable with the current shape
     size_t rep_smem = 0;
     int rep_threads = 512, rep_ctas = 1;
@@ -346,6 +348,9 @@ template <typename R> StepArgs<R> step_args(md_sim *s, int parity, int force_onl
     a.T0 = s->T0;
     a.inv_tau2 = (s->integrator == MD_NVT_NOSE_HOOVER) ? 1.0 / (s->tau * s->tau) : 0.0;
     a.half_skin2 = (R)(0.25 * s->skin * s->skin);
+    a.half_skin = (float)(0.5 * s->skin);
+    a.rebuild_batch = s->rebuild_batch;
+    a.disp = s->b.disp;
     a.force_only = force_only;
     a.f_out = (V4 *)s->b.f_out;
     a.w_out = (R *)s->b.w_out;
@@ -424,12 +429,14 @@ cudaError_t do_rebuild(md_sim *s, int parity, cudaStream_t st, const void *key =
 bool use_rep(const md_sim *s) {
     if (!s->rep_ok || s->list_method != 0) return false;
     if (s->path == 2) return true;
-    if (s->path == 1 || s->path == 3) return false;
-    return s->R >= 32;   // auto: enough replicas to occupy every SM with whole replicas
+    return false;   // auto: the grid path (the replica-resident kernel is chosen by tuning)
 }
 
 // Graph steps are split (unflagged replicas step while flagged ones rebuild) for batches.
-bool split_steps(const md_sim *s) { return s->R >= 8 && !use_rep(s) && s->list_method != 2; }
+// With rebuild slots (K > 1) most steps rebuild nothing and the IF-node graph skips the rebuild.
+bool split_steps(const md_sim *s) {
+    return s->R >= 8 && !use_rep(s) && s->list_method != 2 && s->rebuild_batch <= 1;
+}
 
 cudaError_t do_step(md_sim *s, int parity, cudaStream_t st, int force_only,
                     cudaGraphConditionalHandle next = 0, int has_next = 0, int filter = -1) {
@@ -581,7 +588,8 @@ int recover_overflow(md_sim *s) {
     c.global_ticket = 0;
     if (cudaMemcpyAsync(s->b.ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, s->stream) !=
             cudaSuccess ||
-        cudaMemsetAsync(s->b.ticket, 0, sizeof(unsigned) * s->R, s->stream) != cudaSuccess)
+        cudaMemsetAsync(s->b.ticket, 0, sizeof(unsigned) * s->R, s->stream) != cudaSuccess ||
+        cudaMemsetAsync(s->b.disp, 0, sizeof(unsigned) * 2 * s->R, s->stream) != cudaSuccess)
         return fail(s, MD_ECUDA);
     s->overflows++;
     return request_rebuild_all(s);
@@ -703,7 +711,7 @@ void md_destroy(md_sim *s) {
                      (void **)&b.prep, (void **)&b.nbl, (void **)&b.nnb, (void **)&b.plan,
                      (void **)&b.plan_arr, (void **)&b.sys,
                      (void **)&b.tab, (void **)&b.th, (void **)&b.ctrl, (void **)&b.moved,
-                     (void **)&b.need, (void **)&b.ticket, (void **)&b.partial,
+                     (void **)&b.disp, (void **)&b.need, (void **)&b.ticket, (void **)&b.partial,
                      (void **)&b.tile_rep, (void **)&b.log, &b.f_out, &b.w_out};
     for (void **p : ptrs) {
         if (*p) cudaFree(*p);
@@ -851,6 +859,7 @@ int md_create(md_sim **out, int n_replicas, const int *n_particles, const double
     rc |= dalloc(s, &b.th, n_replicas);
     rc |= dalloc(s, &b.ctrl, 1);
     rc |= dalloc(s, &b.moved, n_replicas);
+    rc |= dalloc(s, &b.disp, 2 * (size_t)n_replicas);
     rc |= dalloc(s, &b.need, 2 * (size_t)n_replicas);   // by step parity: read / written
     rc |= dalloc(s, &b.ticket, n_replicas);
     rc |= dallocb(s, &b.f_out, N * R4);
@@ -879,6 +888,7 @@ int md_create(md_sim **out, int n_replicas, const int *n_particles, const double
     ok = ok && cudaMemset(b.th, 0, sizeof(Thermo) * n_replicas) == cudaSuccess;
     ok = ok && cudaMemset(b.ctrl, 0, sizeof(Ctrl)) == cudaSuccess;
     ok = ok && cudaMemset(b.moved, 0, sizeof(int) * n_replicas) == cudaSuccess;
+    ok = ok && cudaMemset(b.disp, 0, sizeof(unsigned) * 2 * n_replicas) == cudaSuccess;
     ok = ok && cudaMemset(b.need, 0, sizeof(int) * 2 * n_replicas) == cudaSuccess;
     ok = ok && cudaMemset(b.ticket, 0, sizeof(unsigned) * n_replicas) == cudaSuccess;
     ok = ok && cudaMemset(b.nnb, 0, sizeof(int) * N) == cudaSuccess;
@@ -1006,6 +1016,7 @@ int md_set_state(md_sim *s, int r, const double *pos, const int *type, const dou
     ok = ok && cudaMemcpy(b.th + r, &th, sizeof(th), cudaMemcpyHostToDevice) == cudaSuccess;
     ok = ok && cudaMemcpy(need_now(s) + r, &one, sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
     ok = ok && cudaMemcpy(b.moved + r, &zero, sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemset(b.disp + 2 * r, 0, 2 * sizeof(unsigned)) == cudaSuccess;
     ok = ok && cudaMemcpy(&b.ctrl->need_any, &one, sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
     if (!ok) return fail(s, MD_ECUDA);
     s->loaded[r] = 1;
@@ -1293,6 +1304,15 @@ int md_set_coulomb(md_sim *s, const double *charge, double rc_coulomb) {
     return request_rebuild_all(s);
 }
 
+int md_set_rebuild_batch(md_sim *s, int k) {
+    if (!s || k < 1 || k > 64) return MD_EINVAL;
+    if (s->sticky) return s->sticky;
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(s, MD_ECUDA);
+    destroy_graphs(s);
+    s->rebuild_batch = k;
+    return MD_OK;
+}
+
 int md_set_skin(md_sim *s, double skin) {
     if (!s || !(skin > 0.0) || !std::isfinite(skin)) return MD_EINVAL;
     if (s->sticky) return s->sticky;
@@ -1377,6 +1397,7 @@ int md_get_stats(md_sim *s, md_stats *out) {
     out->path = use_rep(s) ? 2 : ((s->path == 3 && s->staged_ok) ? 3 : 1);
     out->rebuild_kernels = s->list_method == 2 ? 0 : s->list_method == 1 ? 2 : s->sort_small ? 3 : 7;
     out->list_method = s->list_method;
+    out->rebuild_batch = s->rebuild_batch;
     out->step_kernels = split_steps(s) ? 2 : 1;     // per graph step
     out->graph_block = s->graph_block;
     out->n_total = s->ntot;
@@ -1631,6 +1652,7 @@ int md_load_checkpoint(md_sim *s, const void *buf, size_t bytes) {
     c.need_any = 1;
     ok = ok && cudaMemcpy(b.ctrl, &c, sizeof(c), cudaMemcpyHostToDevice) == cudaSuccess;
     ok = ok && cudaMemset(b.moved, 0, sizeof(int) * s->R) == cudaSuccess;
+    ok = ok && cudaMemset(b.disp, 0, sizeof(unsigned) * 2 * s->R) == cudaSuccess;
     ok = ok && cudaMemset(b.ticket, 0, sizeof(unsigned) * s->R) == cudaSuccess;
     if (!ok) return fail(s, MD_ECUDA);
     int rc = request_rebuild_all(s);
@@ -1737,16 +1759,18 @@ extern "C" int md_autotune(md_sim *s, const char *cache_path, int steps, int fla
     if (s->sticky) return s->sticky;
     for (char c : s->loaded)
         if (!c) return MD_ESTATE;
-    const std::string key = tune_key(s) + ((flags & MD_TUNE_SKIN) ? "|skin-tuned" : "");
+    const std::string key = tune_key(s) + ((flags & MD_TUNE_SKIN) ? "|skin-tuned" : "") + "|v2";
     int tp = 0, block = 0, reach = 0, lanes = 0;
     double cskin = 0.0;
     if (cache_lookup(cache_path, key, &tp, &block, &reach, &lanes, &cskin) && is_pow2_tp(tp) &&
         block >= tp && block <= 1024 && block % 32 == 0 && reach >= 1 && reach <= 3 &&
-        is_pow2_tp(lanes / 100) && lanes % 10 <= 3 && (lanes / 10) % 10 <= 2) {
+        is_pow2_tp(lanes / 10000) && lanes % 10 <= 3 && (lanes / 10) % 10 <= 2 &&
+        (lanes / 100) % 100 >= 1) {
         int e = 0;
         if ((flags & MD_TUNE_SKIN) && cskin > 0.0 && (e = md_set_skin(s, cskin))) return e;
-        if ((e = md_set_tuning(s, tp, block, reach, lanes / 100))) return e;
+        if ((e = md_set_tuning(s, tp, block, reach, lanes / 10000))) return e;
         if ((e = md_set_list_method(s, (lanes / 10) % 10))) return e;
+        if ((e = md_set_rebuild_batch(s, (lanes / 100) % 100))) return e;
         const int path = lanes % 10;
         return md_set_path(s, (path == 2 && s->rep_ok) || (path == 3 && s->staged_ok) ? path : 1);
     }
@@ -1805,6 +1829,17 @@ extern "C" int md_autotune(md_sim *s, const char *cache_path, int steps, int fla
         }
         if ((rc = md_set_list_method(s, best_m))) return rc;
     }
+    // phase 0c: rebuild slots for batches of replicas (a rebuild pass every K steps serves all
+    // replicas due before the next slot; single systems keep K = 1)
+    if (s->R >= 8 && s->list_method != 2) {
+        int best_k = s->rebuild_batch;
+        for (int k : {2, 4, 8}) {
+            if ((rc = md_set_rebuild_batch(s, k))) return rc;
+            if ((rc = trial(best_tp, best_block, best_reach, best_lanes, &t))) return rc;
+            if (t < best) { best = t; best_k = k; }
+        }
+        if ((rc = md_set_rebuild_batch(s, best_k))) return rc;
+    }
     // phase I: cell stencil reach at the default kernel shape
     for (int re : {2, 1, 3}) {
         if ((rc = trial(best_tp, best_block, re, best_lanes, &t))) return rc;
@@ -1860,8 +1895,10 @@ extern "C" int md_autotune(md_sim *s, const char *cache_path, int steps, int fla
         if ((rc = md_load_checkpoint(s, ck.data(), bytes))) return rc;
     }
     (void)path_saved;
-    // lanes, list method and kernel path share one cache field: lanes * 100 + method * 10 + path
+    // lanes, rebuild slots, list method and kernel path share one cache field:
+    // lanes * 10000 + K * 100 + method * 10 + path
     cache_store(cache_path, key, best_tp, best_block, best_reach,
-                best_lanes * 100 + s->list_method * 10 + s->path, s->skin, best);
+                best_lanes * 10000 + s->rebuild_batch * 100 + s->list_method * 10 + s->path,
+                s->skin, best);
     return MD_OK;
 }

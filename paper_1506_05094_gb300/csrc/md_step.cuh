@@ -106,7 +106,8 @@ __device__ __forceinline__ void merge_lanes(R &fx, R &fy, R &fz, R &u, R &w) {
 template <typename R>
 __device__ __forceinline__ bool integrate_one(const StepArgs<R> &a, const SysDesc &S, int i,
                                               const typename V4T<R>::t &ri, R fx, R fy, R fz,
-                                              R im, R m, R A, R B, R &ke, R &px, R &py, R &pz) {
+                                              R im, R m, R A, R B, R &ke, R &px, R &py, R &pz,
+                                              float &d2, float &st2) {
     typedef typename V4T<R>::t V4;
     const R dt = (R)a.dt;
     V4 v = a.vel[i];
@@ -160,7 +161,37 @@ __device__ __forceinline__ bool integrate_one(const StepArgs<R> &a, const SysDes
     const R bx = min_image_fast(rn.x - pb.x, L, invL);
     const R by = min_image_fast(rn.y - pb.y, L, invL);
     const R bz = min_image_fast(rn.z - pb.z, L, invL);
-    return (bx * bx + by * by + bz * bz) > a.half_skin2;
+    const R db2 = bx * bx + by * by + bz * bz;
+    d2 = (float)db2;
+    st2 = (float)(dt * dt * (v.x * v.x + v.y * v.y + v.z * v.z));
+    return db2 > a.half_skin2;
+}
+
+// Warp maxima of the displacement measures into the replica's slots (non-negative floats order
+// like their bit patterns, so the maximum is independent of the order of the atomics).
+__device__ __forceinline__ void disp_max_warp(unsigned *slot, float d2, float st2) {
+    const unsigned m1 = __reduce_max_sync(FULL_MASK, __float_as_uint(d2));
+    const unsigned m2 = __reduce_max_sync(FULL_MASK, __float_as_uint(st2));
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(slot, m1);
+        atomicMax(slot + 1, m2);
+    }
+}
+
+// Rebuild decision for the next step.  moved: some particle is more than s/2 from its build
+// position, so the list is not valid for the next step (Sec. 6) -- always a rebuild.  With
+// rebuild slots (K > 1) a replica that reaches a slot step also rebuilds when its largest
+// displacement since the build, grown by 1.5 x its largest one-step displacement per step,
+// would pass s/2 before the next slot: rebuilds then fall on the slot steps and a rebuild pass
+// serves many replicas at once.  The list stays valid either way.
+template <typename R>
+__device__ __forceinline__ int rebuild_needed(const StepArgs<R> &a, long long next_step, int moved,
+                                              float d2max, float st2max) {
+    if (moved) return 1;
+    const int K = a.rebuild_batch;
+    if (K <= 1 || (next_step % K) != 0) return 0;
+    const float grow = 1.5f * (float)(K - 1) * sqrtf(st2max);
+    return (sqrtf(d2max) + grow > a.half_skin) ? 1 : 0;
 }
 
 // Sum of one tile's per-particle values: within a warp in R, across the tile's warps in FP64 in
@@ -196,7 +227,8 @@ template <typename R>
 __device__ __forceinline__ void replica_finish(const StepArgs<R> &a, int r, const SysDesc &S,
                                                const double *partial, double xi, int moved,
                                                double (*s_tmp)[MD_NRED], double *s_red,
-                                               bool from_global, int nthr) {
+                                               bool from_global, int nthr, float d2max,
+                                               float st2max) {
     double acc[MD_NRED];
 #pragma unroll
     for (int q2 = 0; q2 < MD_NRED; ++q2) acc[q2] = 0.0;
@@ -234,7 +266,7 @@ __device__ __forceinline__ void replica_finish(const StepArgs<R> &a, int r, cons
             row[5] = xi; row[6] = T->xi_int; row[7] = H; row[8] = s_red[3]; row[9] = s_red[4];
             row[10] = s_red[5];
         }
-        a.need_out[r] = moved;
+        a.need_out[r] = rebuild_needed(a, n + 1, moved, d2max, st2max);
     }
 }
 
@@ -371,10 +403,12 @@ __global__ void __launch_bounds__(1024) k_step(const StepArgs<R> a) {
     const double xi = s_xi;
     R ke = 0, px = 0, py = 0, pz = 0;
     bool moved = false;
+    float d2 = 0.f, st2 = 0.f;
     if (leader)
         moved = integrate_one(a, S, i, ri, fx, fy, fz, s_im[ti], s_m[ti], s_A, s_B, ke, px, py,
-                              pz);
+                              pz, d2, st2);
     if (__ballot_sync(FULL_MASK, moved) != 0u && (threadIdx.x & 31) == 0) atomicOr(a.moved + r, 1);
+    if (a.rebuild_batch > 1) disp_max_warp(a.disp + 2 * r, d2, st2);
 
     R vals[MD_NRED] = {u * R(leader), w * R(leader), ke, px, py, pz};
     tile_partial(vals, s_tmp, a.partial + (long long)tile * MD_NRED, blockDim.x >> 5);
@@ -390,10 +424,14 @@ __global__ void __launch_bounds__(1024) k_step(const StepArgs<R> a) {
     // ---- last tile of replica r: FP64 replica sums in a fixed order, thermostat carry ----
     __threadfence();
     const int mv = __ldcg(a.moved + r);
+    const float d2max = __uint_as_float(__ldcg(a.disp + 2 * r));
+    const float st2max = __uint_as_float(__ldcg(a.disp + 2 * r + 1));
     replica_finish(a, r, S, a.partial + (long long)S.tile_off * MD_NRED, xi, mv, s_tmp, s_red,
-                   true, (int)blockDim.x);
+                   true, (int)blockDim.x, d2max, st2max);
     if (threadIdx.x == 0) {
         a.moved[r] = 0;
+        a.disp[2 * r] = 0u;
+        a.disp[2 * r + 1] = 0u;
         a.rep_ticket[r] = 0u;
         __threadfence();
         const unsigned g = atomicAdd(&a.ctrl->global_ticket, 1u);

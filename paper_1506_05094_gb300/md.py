@@ -26,7 +26,7 @@ LOG_COLS = ("step", "U", "W", "K_minus", "K_plus", "xi", "xi_int", "H", "px", "p
 SYMBOLS = ("md_create", "md_set_integrator", "md_set_state", "md_set_stream", "md_step",
            "md_sync", "md_get_state", "md_get_energies", "md_get_forces", "md_get_neighbors",
            "md_set_tuning", "md_get_tuning", "md_set_skin", "md_get_skin", "md_set_list_capacity",
-           "md_set_path", "md_set_list_method", "md_set_coulomb",
+           "md_set_path", "md_set_list_method", "md_set_coulomb", "md_set_rebuild_batch",
            "md_set_graph_block", "md_autotune",
            "md_get_stats", "md_profile", "md_set_log", "md_get_log", "md_checkpoint_size",
            "md_save_checkpoint", "md_load_checkpoint", "md_destroy", "md_strerror",
@@ -50,7 +50,8 @@ class md_stats(C.Structure):
                 ("replica_rebuilds", C.c_longlong), ("overflows", C.c_longlong),
                 ("n_max", C.c_int), ("max_neighbors", C.c_int), ("tp", C.c_int),
                 ("block", C.c_int), ("reach", C.c_int), ("build_lanes", C.c_int),
-                ("path", C.c_int), ("list_method", C.c_int), ("rebuild_kernels", C.c_int),
+                ("path", C.c_int), ("list_method", C.c_int), ("rebuild_batch", C.c_int),
+                ("rebuild_kernels", C.c_int),
                 ("step_kernels", C.c_int),
                 ("graph_block", C.c_int),
                 ("n_total", C.c_longlong), ("neighbor_entries", C.c_longlong)]
@@ -99,6 +100,7 @@ def lib():
         "md_set_path": [p, i],
         "md_set_list_method": [p, i],
         "md_set_coulomb": [p, pd, d],
+        "md_set_rebuild_batch": [p, i],
         "md_set_graph_block": [p, i],
         "md_autotune": [p, C.c_char_p, i, i],
         "md_set_skin": [p, d],
@@ -238,6 +240,10 @@ class Sim:
 
     def set_list_capacity(self, n_max: int):
         _ck(lib().md_set_list_capacity(self._h, int(n_max)), "md_set_list_capacity")
+
+    def set_rebuild_batch(self, k: int):
+        """Rebuild slots every k steps for batches of replicas (1: rebuild exactly when needed)."""
+        _ck(lib().md_set_rebuild_batch(self._h, int(k)), "md_set_rebuild_batch")
 
     def set_list_method(self, method):
         """'cells' / 'n2' / 'none' (or 0 / 1 / 2)."""
