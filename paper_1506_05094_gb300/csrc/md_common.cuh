@@ -217,6 +217,47 @@ __device__ __forceinline__ void interact(const typename V4T<R>::t &ri, int ti,
     R dx, dy, dz;
     pair_delta(F, ri, rj, dx, dy, dz);
     const R r2 = dx * dx + dy * dy + dz * dz;
+    if (sizeof(R) == 4) {
+        // FP32: branch-free.  Nearly every warp has some lane inside rc, so a branch saves no
+        // work; without it the compiler interleaves the unrolled candidates' arithmetic.  A pair
+        // outside rc contributes exact zeros (the scalar force and energy term are selected to 0).
+        typename Coef4<R>::t c, b;
+        int p = 0;
+        if (SINGLE) {
+            c = c1;
+            b = c1b;
+        } else {
+            p = ti * nt + type_of(rj);
+            c = s_c0[p];
+            b = s_c1[p];
+        }
+        const bool in = r2 < c.x;
+        const R r2i = fast_rcp(r2);
+        const R r6i = r2i * r2i * r2i;
+        R fs = r2i * r6i * (b.x * r6i - b.y);
+        R uu = r6i * (c.y * r6i - c.z) - c.w;
+        if (SF) {
+            const R rinv = fast_rsqrt(r2);
+            fs -= b.z * rinv;
+            uu += (r2 * rinv - b.w) * b.z;
+        }
+        fs = in ? fs : R(0);
+        u += in ? uu : R(0);
+        if (POT & 2) {
+            const typename Coef4<R>::t q = s_cq[p];
+            const bool inq = r2 < q.x;
+            const R rinv = fast_rsqrt(r2);
+            const R fq = rinv * (q.y * rinv * rinv - q.z);
+            const R uq = q.y * rinv - q.w + q.z * (r2 * rinv);
+            fs += inq ? fq : R(0);
+            u += inq ? uq : R(0);
+        }
+        fx += fs * dx;
+        fy += fs * dy;
+        fz += fs * dz;
+        w += fs * r2;
+        return;
+    }
     if (SINGLE) {
         if (r2 < c1.x) lj_pair<SF>(dx, dy, dz, r2, c1, c1b, fx, fy, fz, u, w);
     } else {
