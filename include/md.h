@@ -95,6 +95,7 @@ typedef struct {
     int path;                   /* 1 grid, 2 replica-resident, 3 grid with staged positions */
     int list_method;            /* 0 sorted cells, 1 O(N^2) scan, 2 no list */
     int rebuild_batch;          /* K of md_set_rebuild_batch */
+    int resort;                 /* interval of md_set_resort_interval */
     int rebuild_kernels;        /* kernels launched per rebuild pass on the grid path */
     int step_kernels;           /* step kernels per graph step (2: split around the rebuild) */
     int graph_block;            /* steps per captured CUDA graph (0 = plain launches) */
@@ -198,6 +199,12 @@ int md_set_graph_block(md_sim *sim, int steps);
  * pair rule; forces agree to FP32 summation order.  0 is the default. */
 enum { MD_LIST_CELLS = 0, MD_LIST_N2 = 1, MD_LIST_NONE = 2 };
 int md_set_list_method(md_sim *sim, int method);
+
+/* With the O(N^2) list method: every `passes`-th rebuild pass first sorts the particles by cell
+ * and builds that pass's list from the cells, which keeps neighbours close in memory (Appendix,
+ * step 5: near the crossover to the cell method a sort every few hundred rebuilds can pay).
+ * 0 (default) never sorts; the other list methods ignore it.  MD_EINVAL for passes < 0. */
+int md_set_resort_interval(md_sim *sim, int passes);
 
 /* Shifted-force Coulomb term between charged particles (Sec. 8, the molten-salt benchmark: Coulomb
  * forces with a large shifted-force cutoff instead of a mesh method).  charge[n_types] in units of

@@ -43,7 +43,8 @@ struct SysDesc {
 // Work list of one rebuild pass (written by k_plan): the replicas rebuilt and prefix sums of
 // their particle and cell counts (arrays plan_rep, plan_pp, plan_pc).
 struct Plan {
-    int nflag, tot_p, tot_c, pad;
+    int nflag, tot_p, tot_c;
+    int sort_now;   // O(N^2) method: this pass sorts by cell and builds from the cells
 };
 
 // Per type-pair LJ table (shifted potential, Sec. 2).
@@ -170,6 +171,7 @@ template <typename R> struct RebuildArgs {
     size_t sort_smem;
     int launch_prio;         // host side: CUDA launch priority of these launches (0 = default)
     int list_method;         // 0 sorted cells (Sec. 7), 1 O(N^2) scan (Sec. 6)
+    int resort;              // O(N^2) method: every resort-th pass sorts by cell (0 never)
     const SysDesc *sys;
     const PairTab *tab;
     int ntypes;

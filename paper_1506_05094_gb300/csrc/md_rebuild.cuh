@@ -15,6 +15,12 @@ __device__ __forceinline__ bool rebuild_off(const Ctrl *c) {
     return *(volatile const int *)&c->halt || !*(volatile const int *)&c->need_any;
 }
 
+// The cell sort and the cell-list build run in this pass: always with the cell method, and with
+// the O(N^2) method only on its periodic re-sort passes (Appendix, step 5).
+template <typename A> __device__ __forceinline__ bool cells_off(const A &a) {
+    return rebuild_off(a.ctrl) || (a.list_method == 1 && !a.plan->sort_now);
+}
+
 // largest k in [0, n) with pfx[k] <= t  (pfx ascending, pfx[0] = 0)
 __device__ __forceinline__ int find_seg(const int *pfx, int n, int t) {
     int lo = 0, hi = n - 1;
@@ -41,7 +47,9 @@ template <typename R> __global__ void k_plan(const RebuildArgs<R> a) {
     __shared__ int s_w[3][32];
     const int R_ = a.nrep, nt = blockDim.x;
     if (rebuild_off(a.ctrl)) {
-        if (threadIdx.x == 0) { a.plan->nflag = 0; a.plan->tot_p = 0; a.plan->tot_c = 0; }
+        if (threadIdx.x == 0) {
+            a.plan->nflag = 0; a.plan->tot_p = 0; a.plan->tot_c = 0; a.plan->sort_now = 0;
+        }
         return;
     }
     const int chunk = (R_ + nt - 1) / nt;
@@ -95,7 +103,13 @@ template <typename R> __global__ void k_plan(const RebuildArgs<R> a) {
         a.plan->tot_c = oc;
         a.plan_pp[of] = op;
         a.plan_pc[of] = oc;
-        if (of > 0) a.ctrl->rebuild_passes += 1;
+        int sort_now = 0;
+        if (of > 0) {
+            const int passes = a.ctrl->rebuild_passes + 1;
+            a.ctrl->rebuild_passes = passes;
+            sort_now = (a.list_method == 1 && a.resort > 0 && passes % a.resort == 0) ? 1 : 0;
+        }
+        a.plan->sort_now = sort_now;
     }
 }
 
@@ -108,7 +122,7 @@ __device__ __forceinline__ void pass_particle(const int *pp, const int *rep, int
 }
 
 template <typename R> __global__ void k_bin(const RebuildArgs<R> a) {
-    if (rebuild_off(a.ctrl)) return;
+    if (cells_off(a)) return;
     const int tot = a.plan->tot_p, nf = a.plan->nflag;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
         int r, i;
@@ -122,7 +136,7 @@ template <typename R> __global__ void k_bin(const RebuildArgs<R> a) {
 
 // Per replica: exclusive scan of the cell counts -> cellStart (Sec. 7); counts re-zeroed.
 template <typename R> __global__ void k_scan(const RebuildArgs<R> a) {
-    if (rebuild_off(a.ctrl)) return;
+    if (cells_off(a)) return;
     __shared__ int s_warp[32];
     const int nf = a.plan->nflag;
     for (int b = blockIdx.x; b < nf; b += gridDim.x) {
@@ -166,7 +180,7 @@ template <typename R> __global__ void k_scan(const RebuildArgs<R> a) {
 }
 
 template <typename R> __global__ void k_scatter(const RebuildArgs<R> a) {
-    if (rebuild_off(a.ctrl)) return;
+    if (cells_off(a)) return;
     const int tot = a.plan->tot_p, nf = a.plan->nflag;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
         int r, i;
@@ -178,7 +192,7 @@ template <typename R> __global__ void k_scatter(const RebuildArgs<R> a) {
 // Atomic slot order inside a cell is arbitrary (as with atomicInc in Sec. 6); restore a
 // deterministic order: by user id.
 template <typename R> __global__ void k_cellsort(const RebuildArgs<R> a) {
-    if (rebuild_off(a.ctrl)) return;
+    if (cells_off(a)) return;
     const int tot = a.plan->tot_c, nf = a.plan->nflag;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
         const int k = find_seg(a.plan_pc, nf, t);
@@ -198,7 +212,7 @@ template <typename R> __global__ void k_cellsort(const RebuildArgs<R> a) {
 }
 
 template <typename R> __global__ void k_gather(const RebuildArgs<R> a) {
-    if (rebuild_off(a.ctrl)) return;
+    if (cells_off(a)) return;
     const int tot = a.plan->tot_p, nf = a.plan->nflag;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
         int r, s;
@@ -349,7 +363,7 @@ struct GlobalStart {   // cell starts of replica S in the global cellStart array
 
 template <typename R, int TPB> __global__ void __launch_bounds__(MD_BUILD_BLOCK) k_build(const RebuildArgs<R> a) {
     typedef typename V4T<R>::t V4;
-    if (rebuild_off(a.ctrl)) return;
+    if (cells_off(a)) return;
     __shared__ R s_thr[MD_MAX_PAIRS];
     __shared__ int2 s_rng_all[MD_BUILD_BLOCK / TPB][MD_MAX_RANGES];
     const int npair = a.ntypes * a.ntypes;
@@ -394,7 +408,7 @@ template <typename R, int TPB> __global__ void __launch_bounds__(MD_BUILD_BLOCK)
 template <typename R, int TPB>
 __global__ void __launch_bounds__(MD_BUILD_BLOCK) k_build_n2(const RebuildArgs<R> a) {
     typedef typename V4T<R>::t V4;
-    if (rebuild_off(a.ctrl)) return;
+    if (rebuild_off(a.ctrl) || a.plan->sort_now) return;   // re-sort passes build from cells
     __shared__ R s_thr[MD_MAX_PAIRS];
     const int npair = a.ntypes * a.ntypes;
     for (int p = threadIdx.x; p < npair; p += blockDim.x)

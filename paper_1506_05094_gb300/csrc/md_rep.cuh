@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(1024) k_rep(const StepArgs<R> a, const Rebuild
 template <typename R> __global__ void __launch_bounds__(1024) k_sort_small(const RebuildArgs<R> a) {
     extern __shared__ __align__(16) int sm[];
     __shared__ int s_warp[32];
-    if (rebuild_off(a.ctrl)) return;
+    if (cells_off(a)) return;
     int *s_cnt = sm;                          // sort_cmax
     int *s_cs = s_cnt + a.sort_cmax;          // sort_cmax + 1
     int *s_cell = s_cs + a.sort_cmax + 1;     // sort_nmax

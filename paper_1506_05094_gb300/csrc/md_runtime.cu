@@ -68,6 +68,7 @@ struct md_sim {
     int path = 0;            // 0 auto, 1 grid, 2 replica-resident
     int list_method = 0;     // 0 sorted cells, 1 O(N^2) scan, 2 no list
     int rebuild_batch = 1;   // K: rebuild slots every K steps (1: rebuild exactly when needed)
+    int resort = 0;          // O(N^2) method: sort by cell every resort-th rebuild pass (0 never)
     bool rep_ok = false;     // replica-resident kernel usable with the current shape
     size_t rep_smem = 0;
     int rep_threads = 512, rep_ctas = 1;
@@ -398,6 +399,7 @@ template <typename R> RebuildArgs<R> rebuild_args(md_sim *s, int parity, const v
     a.tpb = s->tpb;
     a.sort_small = s->sort_small ? 1 : 0;
     a.list_method = s->list_method == 1 ? 1 : 0;
+    a.resort = s->list_method == 1 ? s->resort : 0;
     a.sort_nmax = s->rep_nmax;
     a.sort_cmax = s->rep_cmax;
     a.sort_smem = s->sort_smem;
@@ -1304,6 +1306,15 @@ int md_set_coulomb(md_sim *s, const double *charge, double rc_coulomb) {
     return request_rebuild_all(s);
 }
 
+int md_set_resort_interval(md_sim *s, int passes) {
+    if (!s || passes < 0) return MD_EINVAL;
+    if (s->sticky) return s->sticky;
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(s, MD_ECUDA);
+    destroy_graphs(s);
+    s->resort = passes;
+    return MD_OK;
+}
+
 int md_set_rebuild_batch(md_sim *s, int k) {
     if (!s || k < 1 || k > 64) return MD_EINVAL;
     if (s->sticky) return s->sticky;
@@ -1395,9 +1406,14 @@ int md_get_stats(md_sim *s, md_stats *out) {
     out->reach = s->reach;
     out->build_lanes = s->tpb;
     out->path = use_rep(s) ? 2 : ((s->path == 3 && s->staged_ok) ? 3 : 1);
-    out->rebuild_kernels = s->list_method == 2 ? 0 : s->list_method == 1 ? 2 : s->sort_small ? 3 : 7;
+    const int cell_kernels = s->sort_small ? 3 : 7;   // plan, sort (1 or 5 kernels), build
+    out->rebuild_kernels = s->list_method == 2   ? 0
+                           : s->list_method == 0 ? cell_kernels
+                           : s->resort > 0       ? cell_kernels + 1
+                                                 : 2;
     out->list_method = s->list_method;
     out->rebuild_batch = s->rebuild_batch;
+    out->resort = s->resort;
     out->step_kernels = split_steps(s) ? 2 : 1;     // per graph step
     out->graph_block = s->graph_block;
     out->n_total = s->ntot;
@@ -1724,7 +1740,7 @@ std::string tune_key(md_sim *s) {
 }
 
 bool cache_lookup(const char *path, const std::string &key, int *tp, int *block, int *reach,
-                  int *lanes, double *skin) {
+                  int *lanes, double *skin, int *resort) {
     if (!path) return false;
     FILE *f = std::fopen(path, "r");
     if (!f) return false;
@@ -1732,10 +1748,12 @@ bool cache_lookup(const char *path, const std::string &key, int *tp, int *block,
     bool found = false;
     while (std::fgets(line, sizeof(line), f)) {
         char k[900];
-        int a, b, c, d;
-        double sk = 0.0;
-        if (std::sscanf(line, "%899s %d %d %d %d %lf", k, &a, &b, &c, &d, &sk) == 6 && key == k) {
-            *tp = a; *block = b; *reach = c; *lanes = d; *skin = sk;
+        int a, b, c, d, rs = 0;
+        double sk = 0.0, ms = 0.0;
+        if (std::sscanf(line, "%899s %d %d %d %d %lf %lf %d", k, &a, &b, &c, &d, &sk, &ms, &rs) ==
+                8 &&
+            key == k) {
+            *tp = a; *block = b; *reach = c; *lanes = d; *skin = sk; *resort = rs;
             found = true;   // the last entry for a key wins
         }
     }
@@ -1744,11 +1762,12 @@ bool cache_lookup(const char *path, const std::string &key, int *tp, int *block,
 }
 
 void cache_store(const char *path, const std::string &key, int tp, int block, int reach, int lanes,
-                 double skin, double ms) {
+                 double skin, double ms, int resort) {
     if (!path) return;
     FILE *f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "%s %d %d %d %d %.9g %.6f\n", key.c_str(), tp, block, reach, lanes, skin, ms);
+    std::fprintf(f, "%s %d %d %d %d %.9g %.6f %d\n", key.c_str(), tp, block, reach, lanes, skin, ms,
+                 resort);
     std::fclose(f);
 }
 
@@ -1759,10 +1778,11 @@ extern "C" int md_autotune(md_sim *s, const char *cache_path, int steps, int fla
     if (s->sticky) return s->sticky;
     for (char c : s->loaded)
         if (!c) return MD_ESTATE;
-    const std::string key = tune_key(s) + ((flags & MD_TUNE_SKIN) ? "|skin-tuned" : "") + "|v2";
-    int tp = 0, block = 0, reach = 0, lanes = 0;
+    const std::string key = tune_key(s) + ((flags & MD_TUNE_SKIN) ? "|skin-tuned" : "") + "|v3";
+    int tp = 0, block = 0, reach = 0, lanes = 0, cresort = 0;
     double cskin = 0.0;
-    if (cache_lookup(cache_path, key, &tp, &block, &reach, &lanes, &cskin) && is_pow2_tp(tp) &&
+    if (cache_lookup(cache_path, key, &tp, &block, &reach, &lanes, &cskin, &cresort) &&
+        is_pow2_tp(tp) && cresort >= 0 &&
         block >= tp && block <= 1024 && block % 32 == 0 && reach >= 1 && reach <= 3 &&
         is_pow2_tp(lanes / 10000) && lanes % 10 <= 3 && (lanes / 10) % 10 <= 2 &&
         (lanes / 100) % 100 >= 1) {
@@ -1771,6 +1791,7 @@ extern "C" int md_autotune(md_sim *s, const char *cache_path, int steps, int fla
         if ((e = md_set_tuning(s, tp, block, reach, lanes / 10000))) return e;
         if ((e = md_set_list_method(s, (lanes / 10) % 10))) return e;
         if ((e = md_set_rebuild_batch(s, (lanes / 100) % 100))) return e;
+        if ((e = md_set_resort_interval(s, cresort))) return e;
         const int path = lanes % 10;
         return md_set_path(s, (path == 2 && s->rep_ok) || (path == 3 && s->staged_ok) ? path : 1);
     }
@@ -1828,6 +1849,17 @@ extern "C" int md_autotune(md_sim *s, const char *cache_path, int steps, int fla
             if (t < best) { best = t; best_m = m; }
         }
         if ((rc = md_set_list_method(s, best_m))) return rc;
+        // Appendix step 5: with the O(N^2) method, a sort by cell every few hundred rebuilds
+        // can still pay (near the crossover to the cell method); find the interval
+        if (best_m == 1) {
+            int best_rs = 0;
+            for (int rs : {10, 50, 200}) {
+                if ((rc = md_set_resort_interval(s, rs))) return rc;
+                if ((rc = trial(best_tp, best_block, best_reach, best_lanes, &t))) return rc;
+                if (t < best) { best = t; best_rs = rs; }
+            }
+            if ((rc = md_set_resort_interval(s, best_rs))) return rc;
+        }
     }
     // phase 0c: rebuild slots for batches of replicas (a rebuild pass every K steps serves all
     // replicas due before the next slot; single systems keep K = 1)
@@ -1899,6 +1931,6 @@ extern "C" int md_autotune(md_sim *s, const char *cache_path, int steps, int fla
     // lanes * 10000 + K * 100 + method * 10 + path
     cache_store(cache_path, key, best_tp, best_block, best_reach,
                 best_lanes * 10000 + s->rebuild_batch * 100 + s->list_method * 10 + s->path,
-                s->skin, best);
+                s->skin, best, s->resort);
     return MD_OK;
 }

@@ -27,6 +27,7 @@ SYMBOLS = ("md_create", "md_set_integrator", "md_set_state", "md_set_stream", "m
            "md_sync", "md_get_state", "md_get_energies", "md_get_forces", "md_get_neighbors",
            "md_set_tuning", "md_get_tuning", "md_set_skin", "md_get_skin", "md_set_list_capacity",
            "md_set_path", "md_set_list_method", "md_set_coulomb", "md_set_rebuild_batch",
+           "md_set_resort_interval",
            "md_set_graph_block", "md_autotune",
            "md_get_stats", "md_profile", "md_set_log", "md_get_log", "md_checkpoint_size",
            "md_save_checkpoint", "md_load_checkpoint", "md_destroy", "md_strerror",
@@ -51,6 +52,7 @@ class md_stats(C.Structure):
                 ("n_max", C.c_int), ("max_neighbors", C.c_int), ("tp", C.c_int),
                 ("block", C.c_int), ("reach", C.c_int), ("build_lanes", C.c_int),
                 ("path", C.c_int), ("list_method", C.c_int), ("rebuild_batch", C.c_int),
+                ("resort", C.c_int),
                 ("rebuild_kernels", C.c_int),
                 ("step_kernels", C.c_int),
                 ("graph_block", C.c_int),
@@ -101,6 +103,7 @@ def lib():
         "md_set_list_method": [p, i],
         "md_set_coulomb": [p, pd, d],
         "md_set_rebuild_batch": [p, i],
+        "md_set_resort_interval": [p, i],
         "md_set_graph_block": [p, i],
         "md_autotune": [p, C.c_char_p, i, i],
         "md_set_skin": [p, d],
@@ -244,6 +247,10 @@ class Sim:
     def set_rebuild_batch(self, k: int):
         """Rebuild slots every k steps for batches of replicas (1: rebuild exactly when needed)."""
         _ck(lib().md_set_rebuild_batch(self._h, int(k)), "md_set_rebuild_batch")
+
+    def set_resort_interval(self, passes: int):
+        """O(N^2) list method: sort by cell every `passes` rebuild passes (0: never)."""
+        _ck(lib().md_set_resort_interval(self._h, int(passes)), "md_set_resort_interval")
 
     def set_list_method(self, method):
         """'cells' / 'n2' / 'none' (or 0 / 1 / 2)."""

@@ -182,3 +182,51 @@ def test_autotune_chooses_among_list_methods(tmp_path):
         assert sim2.autotune(str(cache), steps_per_trial=20) == tuned
         assert sim2.stats()["list_method"] == method
     print(f"autotune N=500: tuning {tuned}, list method {method}")
+
+
+def test_n2_resort_every_pass_equals_the_cell_method():
+    """With a re-sort on every pass the O(N^2) method builds every list from the sorted cells, so
+    its trajectory is the cell method's bit for bit (Appendix, step 5)."""
+    sts = _ensemble([700, 1000, 600], seed0=740)
+    outs = []
+    for method, resort in (("n2", 1), ("cells", 0)):
+        with make_sim(KA, sts, integrator="nvt", dt=0.0025, T=0.8, graph_block=10) as sim:
+            sim.set_list_method(method)
+            sim.set_resort_interval(resort)
+            sim.step(150)
+            s = sim.stats()
+            assert s["resort"] == resort
+            outs.append([sim.get_state(r) for r in range(len(sts))])
+    for x, y in zip(*outs):
+        for u, v in zip(x, y):
+            np.testing.assert_array_equal(u, v)
+
+
+@pytest.mark.parametrize("graph_block", [0, 10])
+def test_n2_periodic_resort_keeps_lists_exact_and_trajectory(graph_block):
+    sts = _ensemble([800, 1200], seed0=750)
+    with make_sim(KA, sts, integrator="nvt", dt=0.0025, T=0.8, graph_block=graph_block) as sim:
+        sim.set_list_method("n2")
+        sim.set_resort_interval(3)
+        sim.step(100)
+        s = sim.stats()
+        assert s["rebuild_kernels"] >= 4 and s["resort"] == 3
+        for r, st in enumerate(sts):
+            ref = oracle.Run(st.pos, f32(st.vel), st.types, st.L, KA, "nvt", 0.0025, T=0.8)
+            log = ref.run(100)
+            e = sim.energies(r)
+            assert e["U"] == pytest.approx(log[-1, 0], rel=2e-5)
+            x, _ = sim.unwrapped(r)
+            assert np.sqrt(np.mean((x - ref.pos) ** 2)) < 1e-4
+        pos, _, _ = sim.get_state(1)
+    # a fresh build at the final positions (a first build is a sort pass here) against the oracle
+    with make_sim(KA, [sts[1]]) as sim2:
+        sim2.set_list_method("n2")
+        sim2.set_resort_interval(3)
+        sim2.set_state(0, pos, sts[1].types, np.zeros_like(pos))
+        sim2.forces(0)
+        c2, nb2 = sim2.neighbors(0)
+    ref, rc = oracle.neighbors_fp32(f32(pos), sts[1].types, sts[1].L, KA, 0.3)
+    np.testing.assert_array_equal(c2, rc)
+    for i in range(len(pos)):
+        np.testing.assert_array_equal(np.sort(nb2[i, :c2[i]]), ref[i])
