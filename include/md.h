@@ -188,8 +188,9 @@ int md_set_list_capacity(md_sim *sim, int n_max);
 enum { MD_PATH_AUTO = 0, MD_PATH_GRID = 1, MD_PATH_REPLICA = 2, MD_PATH_STAGED = 3 };
 int md_set_path(md_sim *sim, int path);
 
-/* Steps captured per CUDA graph replay (even, >= 2), or 0 for plain kernel launches with
- * device-side early exit of the rebuild kernels (the baseline launch mode). */
+/* Steps captured per CUDA graph replay (>= 1; graphs are kept per starting step parity, so an odd
+ * block uses two), or 0 for plain kernel launches with device-side early exit of the rebuild
+ * kernels (the baseline launch mode).  MD_EINVAL for a negative value. */
 int md_set_graph_block(md_sim *sim, int steps);
 
 /* Neighbour-list method (Appendix phase I): 0 = sorted cells (Sec. 7, Fig. 4: bin, sort all

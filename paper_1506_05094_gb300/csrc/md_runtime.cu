@@ -1372,7 +1372,7 @@ int md_set_path(md_sim *s, int path) {
 
 int md_set_graph_block(md_sim *s, int steps) {
     if (!s) return MD_EINVAL;
-    if (steps < 0 || (steps > 0 && (steps < 2 || (steps & 1)))) return MD_EINVAL;
+    if (steps < 0) return MD_EINVAL;
     if (s->sticky) return s->sticky;
     if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(s, MD_ECUDA);
     destroy_graphs(s);

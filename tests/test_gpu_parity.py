@@ -247,9 +247,12 @@ def _run_bits(st, model, steps, **kw):
     return pos, img, vel, e
 
 
-def test_graph_and_plain_launches_bit_identical():
+@pytest.mark.parametrize("gb", [50, 1, 3])
+def test_graph_and_plain_launches_bit_identical(gb):
+    """Graph blocks of any length (odd ones alternate two graphs, one per starting step parity)
+    give the bits of plain launches."""
     st = ka(900, seed=23)
-    a = _run_bits(st, KA, 200, integrator="nvt", dt=0.0025, T=0.8, graph_block=50)
+    a = _run_bits(st, KA, 200, integrator="nvt", dt=0.0025, T=0.8, graph_block=gb)
     b = _run_bits(st, KA, 200, integrator="nvt", dt=0.0025, T=0.8, graph_block=0)
     for x, y in zip(a[:3], b[:3]):
         np.testing.assert_array_equal(x, y)
