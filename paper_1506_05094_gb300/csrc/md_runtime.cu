@@ -619,7 +619,12 @@ int ensure_list(md_sim *s) {
         int rc = read_ctrl(s);
         if (rc) return rc;
         if (s->h_ctrl->unstable) return fail(s, MD_EUNSTABLE);
-        if (!s->h_ctrl->overflow) return MD_OK;
+        if (!s->h_ctrl->overflow) {
+            // the lists are fresh for the current positions: the next step need not rebuild
+            if (cudaMemsetAsync(need_now(s), 0, sizeof(int) * s->R, s->stream) != cudaSuccess)
+                return fail(s, MD_ECUDA);
+            return MD_OK;
+        }
         if ((rc = recover_overflow(s))) return rc;
     }
     return fail(s, MD_ECUDA);
