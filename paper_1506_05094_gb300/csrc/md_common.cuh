@@ -221,22 +221,24 @@ __device__ __forceinline__ void interact(const typename V4T<R>::t &ri, int ti,
         // FP32: branch-free.  Nearly every warp has some lane inside rc, so a branch saves no
         // work; without it the compiler interleaves the unrolled candidates' arithmetic.  A pair
         // outside rc contributes exact zeros (the scalar force and energy term are selected to 0).
-        typename Coef4<R>::t c, b;
+        // The shifted-potential terms need only c = {rc2, c12, c6, ushift}: with a12 = 12 c12 and
+        // a6 = 6 c6, F = 6 r^-2 r^-6 (2 c12 r^-6 - c6) r_ij, so one shared-memory load per pair.
+        typename Coef4<R>::t c;
         int p = 0;
         if (SINGLE) {
             c = c1;
-            b = c1b;
         } else {
             p = ti * nt + type_of(rj);
             c = s_c0[p];
-            b = s_c1[p];
         }
         const bool in = r2 < c.x;
         const R r2i = fast_rcp(r2);
         const R r6i = r2i * r2i * r2i;
-        R fs = r2i * r6i * (b.x * r6i - b.y);
-        R uu = r6i * (c.y * r6i - c.z) - c.w;
+        const R t = c.y * r6i - c.z;                    // c12 r^-6 - c6
+        R uu = r6i * t - c.w;
+        R fs = (R(6) * r2i) * r6i * (c.y * r6i + t);    // 6 r^-8 (2 c12 r^-6 - c6)
         if (SF) {
+            const typename Coef4<R>::t b = SINGLE ? c1b : s_c1[p];
             const R rinv = fast_rsqrt(r2);
             fs -= b.z * rinv;
             uu += (r2 * rinv - b.w) * b.z;
