@@ -44,16 +44,16 @@ import synth  # noqa: E402
 METRIC = "particle-timesteps/s (single system & batched replicas) vs plain launches, 1 GB300"
 WORKLOAD_NAMES = {
     "ka_ensemble512": "KA ensemble: 512 replicas, N_r~U{512..4096} seed 1004, rho=1.2, "
-                      "NVT T=0.8 dt=0.0025 skin=0.3",
-    "ka8000": "KA N=8000 rho=1.2, NVT T=0.44 dt=0.0025 skin=0.3",
-    "lj131072": "LJ N=131072 fcc rho=0.8442, NVE T=0.72 dt=0.005 skin=0.3",
-    "lj1000": "LJ N=1000 fcc rho=0.8442, NVE T=0.72 dt=0.005 skin=0.3",
+                      "NVT T=0.8 dt=0.0025 skin=0.3 (start value; the autotuner tunes it)",
+    "ka8000": "KA N=8000 rho=1.2, NVT T=0.44 dt=0.0025 skin=0.3 (start value; the autotuner tunes it)",
+    "lj131072": "LJ N=131072 fcc rho=0.8442, NVE T=0.72 dt=0.005 skin=0.3 (start value; the autotuner tunes it)",
+    "lj1000": "LJ N=1000 fcc rho=0.8442, NVE T=0.72 dt=0.005 skin=0.3 (start value; the autotuner tunes it)",
     "salt2000": "molten salt N=2000 (charged LJ, q=+-1, Coulomb SF rc=6.0) rho=0.3677, "
-                "NVT T=2 dt=0.004 skin=0.3",
+                "NVT T=2 dt=0.004 skin=0.3 (start value; the autotuner tunes it)",
     "salt20000": "molten salt N=20000 (charged LJ, q=+-1, Coulomb SF rc=6.0) rho=0.3677, "
-                 "NVT T=2 dt=0.004 skin=0.3",
+                 "NVT T=2 dt=0.004 skin=0.3 (start value; the autotuner tunes it)",
     "salt100000": "molten salt N=100000 (charged LJ, q=+-1, Coulomb SF rc=6.0) rho=0.3677, "
-                  "NVT T=2 dt=0.004 skin=0.3",
+                  "NVT T=2 dt=0.004 skin=0.3 (start value; the autotuner tunes it)",
 }
 L2_BYTES = 129e6
 UNIT = "particle-steps/s"
@@ -428,7 +428,8 @@ def main():
         sim.set_tuning(*tuning)
         tuning = sim.get_tuning()
     else:
-        tuning = sim.autotune(os.path.join(ROOT, "paper_1506_05094_gb300", "tune_cache.txt"), 50)
+        tuning = sim.autotune(os.path.join(ROOT, "paper_1506_05094_gb300", "tune_cache.txt"), 50,
+                              tune_skin=True)
     if args.path:
         sim.set_path(args.path)
     path = {1: "grid", 2: "replica", 3: "staged"}[sim.stats()["path"]]
@@ -569,6 +570,7 @@ def main():
                            "kernel_path": path,
                            "list_method": ["cells", "n2", "none"][st1["list_method"]],
                            "rebuild_slots_K": st1["rebuild_batch"],
+                           "skin": round(sim.skin, 4),
                            "precision": "FP32 pair math, FP64 positions and reductions",
                            "l2": ("flushed: 256 MB written before every timed step "
                                   "(working set %.1f MB < 129 MB L2; one-step graphs)"
