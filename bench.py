@@ -325,6 +325,33 @@ def cpu_baseline(wl, max_seconds=15.0):
             "seconds": spent}
 
 
+def cpu_single_systems(max_seconds=4.0):
+    """The FP64 oracle on the single-system LJ workloads, on all host cores and on one: the plain
+    O(N^2) definition for N = 1000 and the linked-cell mode (equal to it, pinned in the oracle
+    tests) for N = 131072.  Each leg runs steps until about max_seconds have passed."""
+    import oracle
+
+    out = []
+    all_threads = oracle.threads()
+    for name, cells in (("lj1000", False), ("lj131072", True)):
+        wl = synth.workload(name)
+        s = wl.states[0]
+        for threads in (all_threads, 1):
+            oracle.set_threads(threads)
+            run = oracle.Run(s.pos, s.vel, s.types, s.L, wl.model, wl.integrator, wl.dt, T=wl.T,
+                             tau=wl.tau, cells=cells)
+            run.run(1)
+            done, t0 = 0, time.perf_counter()
+            while time.perf_counter() - t0 < max_seconds:
+                run.run(1)
+                done += 1
+            sec = time.perf_counter() - t0
+            out.append({"workload": name, "kind": "oracle " + ("linked cells" if cells else "O(N^2)"),
+                        "cores": threads, "steps": done, "value": s.n * done / sec, "unit": UNIT})
+    oracle.set_threads(all_threads)
+    return out
+
+
 # ------------------------------------------------------------------------------ reference arm
 
 def run_reference(args, max_seconds=120.0):
@@ -557,6 +584,7 @@ def main():
                                    for w in ("ka8000", "lj131072", "salt20000")
                                    if w != args.workload]
         extras["cpu_baseline"] = cpu_baseline(wl)
+        extras["cpu_single_systems"] = cpu_single_systems()
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,

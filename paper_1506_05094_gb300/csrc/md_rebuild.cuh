@@ -451,7 +451,9 @@ __global__ void __launch_bounds__(MD_BUILD_BLOCK) k_build_n2(const RebuildArgs<R
                 cnt = a.nmax;
             }
             a.nnb[i] = cnt;
-            a.pos_build[i] = ki;
+            // build positions = the keys; not rewritten when the keys are the build positions
+            // themselves (other groups are still reading them)
+            if (a.key != a.pos_build) a.pos_build[i] = ki;
             if (S.off == i) a.th[r].rebuilds += 1;
         }
     }
