@@ -558,7 +558,9 @@ int build_graph(md_sim *s, int p) {
         return fail(s, MD_ECUDA);
     }
     cudaGraphExec_t ex = nullptr;
-    if (cudaGraphInstantiate(&ex, out, 0) != cudaSuccess) {
+    // the launch priorities captured into the nodes (rebuild branch above the step of the
+    // replicas that keep their list) apply only with this flag
+    if (cudaGraphInstantiate(&ex, out, cudaGraphInstantiateFlagUseNodePriority) != cudaSuccess) {
         cudaGraphDestroy(out);
         return fail(s, MD_ECUDA);
     }
