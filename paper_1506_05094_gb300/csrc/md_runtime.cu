@@ -1834,6 +1834,16 @@ extern "C" int md_autotune(md_sim *s, const char *cache_path, int steps, int fla
     };
     int nmax_part = 0;
     for (int v : s->n) nmax_part = std::max(nmax_part, v);
+    // The Appendix tries only t_p = 1 above 10^5 particles, on its GPU with 15 SMs of 2048 resident
+    // threads; the size from which one thread per particle fills the GPU grows with its resident
+    // threads, so the limit is scaled by this GPU's.
+    int max_thr = 2048;
+    if (cudaDeviceGetAttribute(&max_thr, cudaDevAttrMaxThreadsPerMultiProcessor, s->device) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        max_thr = 2048;
+    }
+    const double tp1_limit = 1e5 * (double)s->nsm * (double)max_thr / (15.0 * 2048.0);
     // Appendix defaults: t_p = 4 (p_b = 32) up to 10^4 particles, else t_p = 1 (p_b = 64)
     int best_tp = nmax_part <= 10000 ? 4 : 1, best_block = nmax_part <= 10000 ? 128 : 64;
     int best_reach = 2, best_lanes = 8;
@@ -1895,7 +1905,7 @@ extern "C" int md_autotune(md_sim *s, const char *cache_path, int steps, int fla
         int worse = 0;
         for (int tpv = 1; tpv <= 32; tpv *= 2) {
             if (tpv > b) break;
-            if (nmax_part > 100000 && tpv > 1) break;   // Appendix: only t_p = 1 for N > 1e5
+            if (nmax_part > tp1_limit && tpv > 1) break;   // Appendix: only t_p = 1 for large N
             if ((rc = trial(tpv, b, best_reach, best_lanes, &t))) return rc;
             if (t < best_b) best_b = t;
             if (t < best) { best = t; best_tp = tpv; best_block = b; worse = 0; continue; }
