@@ -11,9 +11,12 @@
  *   - neighbour list of all pairs within rc + s, column-major, with skin s .. Sec. 4, Sec. 5
  *   - rebuild when any particle moved more than s/2 (device-side flag) ..... Sec. 6 (O(N^2) text)
  *   - cell-index binning, sort of all particle data by cell, list build .... Sec. 7, Fig. 4
+ *   - O(N^2) list build (with an occasional re-sort) and the no-list mode .. Sec. 6, Appendix
  *   - leapfrog NVE and Nose-Hoover NVT integrators .......................... Sec. 2
- *   - shifted-potential cutoff ............................................... Sec. 2
- *   - parameter search over threads per particle, block size, cell size ..... Appendix
+ *   - shifted-potential and shifted-force cutoffs ........................... Sec. 2
+ *   - Coulomb interactions with a shifted-force cutoff ...................... Sec. 8
+ *   - parameter search over list method, skin, threads per particle, block
+ *     size and cell size, with a cache of tuned parameters .................. Appendix
  *
  * Conventions.
  *   - Every function returns an md_status (0 = MD_OK).  Errors are sticky per md_sim: after a
