@@ -41,7 +41,7 @@ def _worker(rank, world, port, out):
 
 def test_two_ranks_weak_scaling_host_logic():
     world, port = 2, _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:   # no fork of a multi-threaded process
         out = m.dict()
         mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
