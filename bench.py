@@ -231,17 +231,29 @@ def pick_block(steps: int) -> int:
     return 2
 
 
-def time_steps(sim, stream_obj, steps: int):
+def time_steps(sim, stream_obj, steps: int, segments: list | None = None, nseg: int = 5,
+               block: int = 1):
+    """Duration of `steps` steps (ms, CUDA events on the sim's stream).  With `segments`, the
+    region is also cut into `nseg` equal parts (whole graph blocks) by events recorded in the same
+    stream, without extra synchronisation, and their durations are appended."""
     import torch
 
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    cut = segments is not None and steps % (nseg * block) == 0
+    n_ev = nseg + 1 if cut else 2
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(n_ev)]
     torch.cuda.synchronize()
-    e0.record(stream_obj)
-    sim.step(steps)
-    e1.record(stream_obj)
-    e1.synchronize()
-    return e0.elapsed_time(e1)
+    ev[0].record(stream_obj)
+    if cut:
+        for k in range(nseg):
+            sim.step(steps // nseg)
+            ev[k + 1].record(stream_obj)
+    else:
+        sim.step(steps)
+        ev[1].record(stream_obj)
+    ev[-1].synchronize()
+    if cut:
+        segments.extend(ev[k].elapsed_time(ev[k + 1]) for k in range(nseg))
+    return ev[0].elapsed_time(ev[-1])
 
 
 def l2_flush_buffer():
@@ -250,7 +262,7 @@ def l2_flush_buffer():
     return torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
 
-def time_steps_flushed(sim, stream_obj, steps: int):
+def time_steps_flushed(sim, stream_obj, steps: int, per_step: list | None = None):
     """Sum of per-step durations (CUDA events on the sim's stream), the L2 flushed by a 256 MB
     write before every step; each step is one replay of a one-step CUDA graph."""
     import torch
@@ -268,7 +280,10 @@ def time_steps_flushed(sim, stream_obj, steps: int):
         sim.step(1)
         e1.record(stream_obj)
         e1.synchronize()
-        tot += e0.elapsed_time(e1)
+        ms = e0.elapsed_time(e1)
+        tot += ms
+        if per_step is not None:
+            per_step.append(ms)
     del flush
     return tot
 
@@ -477,13 +492,24 @@ def main():
 
     barrier()
     with Clocks(local) as ck:
-        ms = (time_steps_flushed(sim, stream, args.steps) if flushed
-              else time_steps(sim, stream, args.steps))
+        seg = []
+        ms = (time_steps_flushed(sim, stream, args.steps, seg) if flushed
+              else time_steps(sim, stream, args.steps, seg, 5, gb))
     barrier()
     clocks = ck.summary()
     st1 = sim.stats()
     ms_max = rep.max_over_ranks(ms, device="cuda")
     value = rep.job_throughput(n_total, world, args.steps, ms_max)
+    # five repeats inside the timed region: consecutive fifths of the K steps
+    repeats = None
+    if flushed and len(seg) >= 5:
+        q = len(seg) // 5
+        seg = [sum(seg[k * q:(k + 1) * q]) for k in range(5)]
+    if len(seg) == 5:
+        per = [n_total * world * (args.steps / 5) / (t / 1e3) for t in seg]
+        repeats = {"n": 5, "steps_each": args.steps // 5, "best": max(per),
+                   "median": statistics.median(per), "worst": min(per), "unit": UNIT,
+                   "note": "this rank's fifths of the timed steps"}
     passes = st1["rebuild_passes"] - st0["rebuild_passes"]
     # graph replays: one arm kernel + gb step kernels + 6 rebuild kernels per executed IF body;
     # an odd K ends with one plain step (its 6 rebuild kernels launch and exit if not needed)
@@ -606,7 +632,8 @@ def main():
                                  ("no flush: working set %.2f GB (neighbour list) > 129 MB L2"
                                   % (ws_bytes / 1e9)),
                            "parallelism": f"replicas x{world}"},
-                "clocks": clocks, "gpu_launches": gpu_launches, "roofline": roofline}
+                "clocks": clocks, "gpu_launches": gpu_launches, "roofline": roofline,
+                "repeats": repeats}
         line.update(extras)
         if "e2e" not in line:
             line["e2e"] = None
