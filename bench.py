@@ -562,11 +562,12 @@ def main():
                      "rebuild_passes_per_step": prof["rebuild_fraction"]})
 
     extras = {}
-    if rank == 0 and not args.no_extras:
-        # e2e through the C ABI with host buffers: set_state (H2D) -> steps -> energies + state (D2H)
+    if not args.no_extras:
+        # e2e through the C ABI with host buffers, on every rank (the whole job, slowest rank's
+        # wall clock): set_state (H2D) -> steps -> energies + state (D2H)
         sim.set_graph_block(GRAPH_BLOCK)
         host = [(s.pos, s.types, s.vel) for s in wl.states]
-        torch.cuda.synchronize()
+        barrier()
         t0 = time.perf_counter()
         for r, (p, ty, v) in enumerate(host):
             sim.set_state(r, p, ty, v)
@@ -575,13 +576,16 @@ def main():
         outs = [sim.get_state(r) for r in range(len(wl.states))]
         t1 = time.perf_counter()
         del en, outs
+        e2e_ms = rep.max_over_ranks((t1 - t0) * 1e3, device="cuda")
         h2d = n_total * (24 + 4 + 24)
         d2h = n_total * (24 + 12 + 24) + len(wl.states) * 128
-        extras["e2e"] = {"value": n_total * args.steps / (t1 - t0), "unit": UNIT,
-                         "h2d_bytes_per_step": h2d / args.steps,
-                         "d2h_bytes_per_step": d2h / args.steps,
-                         "what": "md_set_state for all replicas, md_step(K), md_get_energies + "
-                                 "md_get_state for all replicas, host wall clock"}
+        extras["e2e"] = {"value": rep.job_throughput(n_total, world, args.steps, e2e_ms),
+                         "unit": UNIT, "h2d_bytes_per_step": h2d * world / args.steps,
+                         "d2h_bytes_per_step": d2h * world / args.steps,
+                         "what": "on every rank: md_set_state for all replicas, md_step(K), "
+                                 "md_get_energies + md_get_state for all replicas; host wall "
+                                 "clock, slowest rank"}
+    if rank == 0 and world == 1 and not args.no_extras:
         # batched vs the same replicas one after another with plain launches
         seq_steps = 20
         from paper_1506_05094_gb300 import Sim
