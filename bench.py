@@ -47,6 +47,7 @@ WORKLOAD_NAMES = {
                       "NVT T=0.8 dt=0.0025 skin=0.3 (start value; the autotuner tunes it)",
     "ka8000": "KA N=8000 rho=1.2, NVT T=0.44 dt=0.0025 skin=0.3 (start value; the autotuner tunes it)",
     "lj131072": "LJ N=131072 fcc rho=0.8442, NVE T=0.72 dt=0.005 skin=0.3 (start value; the autotuner tunes it)",
+    "lj1048576": "LJ N=1048576 fcc rho=0.8442, NVE T=0.72 dt=0.005 skin=0.3 (start value; the autotuner tunes it)",
     "lj1000": "LJ N=1000 fcc rho=0.8442, NVE T=0.72 dt=0.005 skin=0.3 (start value; the autotuner tunes it)",
     "salt2000": "molten salt N=2000 (charged LJ, q=+-1, Coulomb SF rc=6.0) rho=0.3677, "
                 "NVT T=2 dt=0.004 skin=0.3 (start value; the autotuner tunes it)",
@@ -215,20 +216,36 @@ def step_kernel_flops(wl, entries: int, cutoff: str = "sp") -> float:
 
 
 def fp32_peak_tflops(sm_mhz: float, nsm: int = 152) -> float:
-    """FP32 pipe peak from unit counts and the SM clock: SMs x 128 lanes x 2 flop (FMA)."""
+    """FP32 pipe peak from unit counts and the SM clock: SMs x 128 lanes x 2 flop (FMA).  Only
+    the fallback when the measured peak (md_measure_fp32_peak) is unavailable."""
     return nsm * FP32_LANES_PER_SM * 2.0 * sm_mhz * 1e6 / 1e12
 
 
-def pick_block(steps: int) -> int:
-    """Graph block for a timed run of `steps`: 100 when it divides, else the largest even
-    divisor up to 200 (an odd count leaves one plain step)."""
-    if steps % GRAPH_BLOCK == 0:
-        return GRAPH_BLOCK
+def pick_block(steps: int, nseg: int = 5) -> int:
+    """Graph block for a timed run of `steps`: the largest even block up to 100 steps that cuts
+    the run into `nseg` equal segments of whole graphs (so the five repeats can be timed inside
+    the run), else the largest even divisor up to 100 (an odd count leaves one plain step)."""
+    for b in range(min(GRAPH_BLOCK, steps), 1, -1):
+        if b % 2 == 0 and steps % (nseg * b) == 0:
+            return b
     even = steps - (steps & 1)
-    for b in range(min(200, even), 1, -1):
+    for b in range(min(GRAPH_BLOCK, even), 1, -1):
         if b % 2 == 0 and even % b == 0:
             return b
     return 2
+
+
+def prepare_graphs(sim, gb: int) -> None:
+    """Capture the CUDA graphs of both starting step parities before any timed region, so that
+    no timed md_step call builds or instantiates a graph (checked with md_stats.graph_builds)."""
+    sim.set_graph_block(gb)
+    before = sim.stats()["graph_builds"]
+    sim.step(gb)          # graph of the current parity
+    if gb % 2 == 0:
+        sim.step(1)       # one plain step flips the parity
+    sim.step(gb)          # graph of the other parity
+    built = sim.stats()["graph_builds"] - before
+    assert built <= 2, f"expected at most two graph builds, got {built}"
 
 
 def time_steps(sim, stream_obj, steps: int, segments: list | None = None, nseg: int = 5,
@@ -268,8 +285,7 @@ def time_steps_flushed(sim, stream_obj, steps: int, per_step: list | None = None
     import torch
 
     flush = l2_flush_buffer()
-    sim.set_graph_block(1)
-    sim.step(2)                      # capture the graphs of both step parities (untimed)
+    prepare_graphs(sim, 1)           # capture the graphs of both step parities (untimed)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     tot = 0.0
@@ -288,26 +304,59 @@ def time_steps_flushed(sim, stream_obj, steps: int, per_step: list | None = None
     return tot
 
 
-def time_single_system(name, stream_obj, steps, warmup):
-    """Single system, each step timed alone with CUDA events and L2 flushed in between."""
-    import torch
+def step_roofline(sim, wl, peaks, p_fp32, n_prof=50):
+    """Roofline position of the fused step kernel of a workload: md_profile's CUDA-event time of
+    the step kernel (plain launches) against its algorithmic bytes and flops."""
+    prof = sim.profile(n_prof)
+    n_total = wl.n_total
+    bytes_launch = step_kernel_bytes(n_total, prof["neighbor_entries"], "mixed")
+    flops_launch = step_kernel_flops(wl, prof["neighbor_entries"])
+    sec = prof["step_kernel_ms"] * 1e-3
+    hbm = bytes_launch / sec / 1e9
+    alu = flops_launch / sec / 1e12
+    t_hbm = bytes_launch / (peaks["hbm_gbs"] * 1e9)
+    t_alu = flops_launch / (p_fp32 * 1e12)
+    return {"bound": "hbm" if t_hbm >= t_alu else "alu",
+            "frac": max(t_hbm, t_alu) / sec,
+            "hbm": {"achieved": hbm, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": hbm / peaks["hbm_gbs"]},
+            "alu": {"achieved": alu, "peak": p_fp32, "unit": "TFLOP/s", "frac": alu / p_fp32},
+            "step_kernel_ms": prof["step_kernel_ms"], "algorithmic_bytes_per_launch": bytes_launch,
+            "flops_per_launch": flops_launch,
+            "entries_per_particle": prof["neighbor_entries"] / n_total,
+            "rebuild_pass_ms": prof["rebuild_ms"],
+            "rebuild_passes_per_step": prof["rebuild_fraction"]}
 
+
+def time_single_system(name, stream_obj, steps, warmup, peaks=None, p_fp32=None):
+    """Single system.  A working set below the L2 size is timed step by step with the L2 flushed
+    in between (and, for context, as back-to-back graph replays with the L2 warm); a larger one
+    is timed as back-to-back graph replays (no flush needed).  Adds the step kernel's roofline
+    position when peaks are given."""
     wl = synth.workload(name)
     sim = make_sim(wl, stream_obj.cuda_stream)
     sim.autotune(os.path.join(ROOT, "paper_1506_05094_gb300", "tune_cache.txt"), 50)
+    n = wl.n_total
     sim.set_graph_block(1)
     sim.step(max(warmup, 3))
-    tot = time_steps_flushed(sim, stream_obj, steps)
-    # back-to-back graph replay of the same system (L2 stays warm: working set stated)
-    sim.set_graph_block(GRAPH_BLOCK)
+    st0 = sim.stats()
+    ws_bytes = 4.0 * st0["neighbor_entries"] + 100.0 * n
+    out = {"workload": name, "n": n, "working_set_mb": ws_bytes / 1e6}
+    if ws_bytes < L2_BYTES:
+        tot = time_steps_flushed(sim, stream_obj, steps)
+        out.update(ms_per_step_flushed=tot / steps, value_flushed=n * steps / (tot / 1e3))
+    # back-to-back graph replay (L2 warm when the working set fits; stated above)
+    prepare_graphs(sim, GRAPH_BLOCK)
     sim.step(GRAPH_BLOCK)
+    b0 = sim.stats()["graph_builds"]
     ms_graph = time_steps(sim, stream_obj, 10 * GRAPH_BLOCK) / (10 * GRAPH_BLOCK)
+    assert sim.stats()["graph_builds"] == b0
+    key = "l2_warm" if ws_bytes < L2_BYTES else "no_flush_needed"
+    out.update({f"ms_per_step_graph_{key}": ms_graph, f"value_graph_{key}": n / (ms_graph / 1e3)})
+    if peaks is not None:
+        out["roofline"] = step_roofline(sim, wl, peaks, p_fp32)
     st = sim.stats()
-    n = wl.n_total
-    out = {"workload": name, "n": n, "ms_per_step_flushed": tot / steps,
-           "value_flushed": n * steps / (tot / 1e3),
-           "ms_per_step_graph_l2_warm": ms_graph, "value_graph_l2_warm": n / (ms_graph / 1e3),
-           "tuning": list(sim.get_tuning()), "rebuild_passes": st["rebuild_passes"]}
+    out.update(tuning=list(sim.get_tuning()), rebuild_passes=st["rebuild_passes"])
     sim.close()
     return out
 
@@ -476,14 +525,16 @@ def main():
         sim.set_path(args.path)
     path = {1: "grid", 2: "replica", 3: "staged"}[sim.stats()["path"]]
     gb = pick_block(args.steps)
-    sim.set_graph_block(gb)
-    sim.step(gb)                     # capture the graph (setup, untimed)
+    prepare_graphs(sim, gb)          # graphs of both step parities (setup, untimed)
     sim.step(args.warmup)            # warm-up steps, untimed
     st0 = sim.stats()
     # working set of a step: list indices + ~100 B of per-particle state; below the L2 size the
     # steps are timed one by one with the L2 flushed in between
     ws_bytes = 4.0 * st0["neighbor_entries"] + 100.0 * n_total
     flushed = ws_bytes < L2_BYTES
+    if flushed:                      # one-step graphs of both parities, before the timed region
+        prepare_graphs(sim, 1)
+        st0 = sim.stats()
 
     def barrier():
         if world > 1:
@@ -498,6 +549,9 @@ def main():
     barrier()
     clocks = ck.summary()
     st1 = sim.stats()
+    # no graph was captured or instantiated inside the timed region
+    graph_builds_timed = st1["graph_builds"] - st0["graph_builds"]
+    assert graph_builds_timed == 0, graph_builds_timed
     ms_max = rep.max_over_ranks(ms, device="cuda")
     value = rep.job_throughput(n_total, world, args.steps, ms_max)
     # five repeats inside the timed region: consecutive fifths of the K steps
@@ -532,17 +586,25 @@ def main():
     achieved = bytes_launch / (prof["step_kernel_ms"] * 1e-3) / 1e9
     tr = traffic_per_particle()
     traffic = None if tr is None else tr["dram_bytes_per_particle"] * n_total
-    # FP32 pipe bound at the clock sampled during the timed region (max clock if none)
+    # FP32 pipe bound: the FMA throughput measured on this GPU (md_measure_fp32_peak)
     flops_launch = step_kernel_flops(wl, prof["neighbor_entries"])
-    sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    p_fp32 = fp32_peak_tflops(sm_mhz, torch.cuda.get_device_properties(local).multi_processor_count)
+    try:
+        fp32 = mdmod.measure_fp32_peak(stream.cuda_stream, 5)
+        p_fp32 = fp32["tflops"]
+        fp32_kind = ("measured: md_measure_fp32_peak, independent FMA chains on all %d SMs, "
+                     "best of 5 launches of %.2f ms" % (fp32["sms"], fp32["ms"]))
+    except Exception as exc:   # noqa: BLE001 -- report the fallback, never hide it
+        sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+        p_fp32 = fp32_peak_tflops(sm_mhz,
+                                  torch.cuda.get_device_properties(local).multi_processor_count)
+        fp32_kind = ("derived (measurement failed: %s): SMs x 128 FP32 lanes x 2 flop x "
+                     "median SM clock %.0f MHz" % (exc, sm_mhz))
     t_hbm = bytes_launch / (peaks["hbm_gbs"] * 1e9)
     t_alu = flops_launch / (p_fp32 * 1e12)
     alu_achieved = flops_launch / (prof["step_kernel_ms"] * 1e-3) / 1e12
     alu = {"achieved": alu_achieved, "peak": p_fp32, "unit": "TFLOP/s",
            "frac": alu_achieved / p_fp32, "flops_per_launch": flops_launch,
-           "peak_kind": "derived: SMs x 128 FP32 lanes x 2 flop x median SM clock %.0f MHz"
-                        % sm_mhz}
+           "peak_kind": fp32_kind}
     if t_alu > t_hbm:
         roofline = {"bound": "alu", "achieved": alu_achieved, "peak": p_fp32, "unit": "TFLOP/s",
                     "frac": alu_achieved / p_fp32, "traffic": traffic,
@@ -565,7 +627,6 @@ def main():
     if not args.no_extras:
         # e2e through the C ABI with host buffers, on every rank (the whole job, slowest rank's
         # wall clock): set_state (H2D) -> steps -> energies + state (D2H)
-        sim.set_graph_block(GRAPH_BLOCK)
         host = [(s.pos, s.types, s.vel) for s in wl.states]
         barrier()
         t0 = time.perf_counter()
@@ -609,10 +670,11 @@ def main():
         extras["sequential_plain_launches"] = {"value": seq_value, "unit": UNIT,
                                                "steps": seq_steps,
                                                "batched_over_sequential": value / world / seq_value}
-        # single systems
-        extras["single_system"] = [time_single_system(w, stream, 200, args.warmup)
-                                   for w in ("ka8000", "lj131072", "salt20000")
-                                   if w != args.workload]
+        # single systems; the two large LJ systems carry their step kernel's roofline position
+        extras["single_system"] = [
+            time_single_system(w, stream, 200, args.warmup,
+                               *((peaks, p_fp32) if w.startswith("lj") else ()))
+            for w in ("ka8000", "lj131072", "lj1048576", "salt20000") if w != args.workload]
         extras["cpu_baseline"] = cpu_baseline(wl)
         extras["cpu_single_systems"] = cpu_single_systems()
 
@@ -637,7 +699,7 @@ def main():
                                   % (ws_bytes / 1e9)),
                            "parallelism": f"replicas x{world}"},
                 "clocks": clocks, "gpu_launches": gpu_launches, "roofline": roofline,
-                "repeats": repeats}
+                "repeats": repeats, "graph_builds_in_timed_region": graph_builds_timed}
         line.update(extras)
         if "e2e" not in line:
             line["e2e"] = None

@@ -14,7 +14,7 @@
  *   - O(N^2) list build (with an occasional re-sort) and the no-list mode .. Sec. 6, Appendix
  *   - leapfrog NVE and Nose-Hoover NVT integrators .......................... Sec. 2
  *   - shifted-potential and shifted-force cutoffs ........................... Sec. 2
- *   - Coulomb interactions with a shifted-force cutoff ...................... Sec. 8
+ *   - Coulomb interactions with a shifted-force cutoff ...................... Sec. 9
  *   - parameter search over list method, skin, threads per particle, block
  *     size and cell size, with a cache of tuned parameters .................. Appendix
  *
@@ -104,6 +104,9 @@ typedef struct {
     int graph_block;            /* steps per captured CUDA graph (0 = plain launches) */
     long long n_total;          /* particles over all replicas */
     long long neighbor_entries; /* sum of neighbour counts at the most recent build */
+    long long graph_builds;     /* CUDA graphs captured and instantiated so far (a timed region
+                                   that must not include host-side graph construction can
+                                   compare this before and after) */
 } md_stats;
 
 /* Average device durations measured with CUDA events by md_profile (milliseconds). */
@@ -132,13 +135,22 @@ int md_create(md_sim **out, int n_replicas, const int *n_particles, const double
  * tau (friction update xi_n = xi_{n-1} + dt (K_{n-1/2}/K0 - 1)/tau^2, K0 = (3N-3) T / 2). */
 int md_set_integrator(md_sim *sim, int kind, double dt, double T, double tau);
 
-/* Load replica r: pos (n,3) in any periodic image (wrapped into [0,L) here, the wrap added to
- * the image counters), type (n) in [0,n_types), vel (n,3) = v(t - dt/2), image (n,3) or NULL.
- * Resets the replica's thermostat (xi = 0) and step record, and forces a list rebuild. */
+/* Load replica r (Sec. 2, Fig. 1: the simulation object starts from an initial configuration of
+ * positions, types and velocities; here the caller passes it as arrays instead of a file):
+ * pos (n,3) in any periodic image (wrapped into [0,L) here, the wrap added to the image
+ * counters), type (n) in [0,n_types), vel (n,3) = v(t - dt/2) (the leapfrog half step of the
+ * Sec. 2 integrators), image (n,3) or NULL.  Host arrays, copied in; the caller keeps them.
+ * Resets the replica's thermostat (xi = 0) and step record, and forces a list rebuild.
+ * MD_EINVAL for a bad replica index, a NULL array, a type outside [0,n_types) or a non-finite
+ * value (nothing is changed); MD_ECUDA (sticky) if a copy fails. */
 int md_set_state(md_sim *sim, int replica, const double *pos, const int *type, const double *vel,
                  const int *image);
 
-/* Issue all device work on this cudaStream_t (e.g. torch.cuda.current_stream().cuda_stream). */
+/* Issue all device work on this cudaStream_t (e.g. torch.cuda.current_stream().cuda_stream).
+ * The paper runs one simulation per GPU (Sec. 2) and says nothing about streams; this call lets
+ * the caller order the library's kernels with its own work.  The stream stays the caller's (it is
+ * not destroyed); pending work on the previous stream is waited for first.  MD_ECUDA (sticky)
+ * if that wait fails. */
 int md_set_stream(md_sim *sim, void *cuda_stream);
 
 /* Advance all replicas by n_steps >= 0 timesteps (Fig. 2 force kernel fused with the
@@ -147,14 +159,19 @@ int md_set_stream(md_sim *sim, void *cuda_stream);
  * as in Sec. 4.  Returns after the steps completed, or the first sticky error. */
 int md_step(md_sim *sim, long long n_steps);
 
-/* Wait for outstanding work; surfaces sticky device errors. */
+/* Wait for outstanding work on the md_sim's stream (the end of a Sec. 2 / Fig. 1 "Run" of
+ * steps); surfaces sticky device errors (MD_ECUDA, MD_EUNSTABLE). */
 int md_sync(md_sim *sim);
 
-/* Copy replica r out in user order: pos (n,3) wrapped into [0,L), image (n,3), vel (n,3) =
- * v(t - dt/2).  Any pointer may be NULL. */
+/* Copy replica r out in user order (the configuration that Sec. 2 saves to disk, positions with
+ * their periodic images): pos (n,3) wrapped into [0,L), image (n,3), vel (n,3) = v(t - dt/2).
+ * Host arrays owned by the caller; any pointer may be NULL.  MD_ESTATE before md_set_state of
+ * this replica, MD_EINVAL for a bad replica index. */
 int md_get_state(md_sim *sim, int replica, double *pos, int *image, double *vel);
 
-/* Thermodynamic record of replica r (see md_energies). */
+/* Thermodynamic record of replica r (see md_energies): the energy, virial, pressure and
+ * temperature that Sec. 2 lists among RUMD's basic statistics, computed on the device with FP64
+ * reductions at every step.  *out is caller-owned.  MD_EINVAL for a bad index or NULL out. */
 int md_get_energies(md_sim *sim, int replica, md_energies *out);
 
 /* Test hook: forces f (n,3), u_i (n), w_i (n) at the CURRENT positions of replica r (rebuilding
@@ -210,7 +227,7 @@ int md_set_list_method(md_sim *sim, int method);
  * 0 (default) never sorts; the other list methods ignore it.  MD_EINVAL for passes < 0. */
 int md_set_resort_interval(md_sim *sim, int passes);
 
-/* Shifted-force Coulomb term between charged particles (Sec. 8, the molten-salt benchmark: Coulomb
+/* Shifted-force Coulomb term between charged particles (Sec. 9, the molten-salt benchmark: Coulomb
  * forces with a large shifted-force cutoff instead of a mesh method).  charge[n_types] in units of
  * sqrt(4 pi eps0 eps sigma) (the paper's reduced units), rc_coulomb the Coulomb cutoff rc_C:
  *   u_C(r) = q_a q_b (1/r - 1/rc_C + (r - rc_C)/rc_C^2),  F_ij = q_a q_b (1/r^2 - 1/rc_C^2) r_ij/r
@@ -270,20 +287,37 @@ int md_checkpoint_size(md_sim *sim, size_t *bytes);
 int md_save_checkpoint(md_sim *sim, void *buf, size_t bytes);
 int md_load_checkpoint(md_sim *sim, const void *buf, size_t bytes);
 
+/* Free every device and host buffer of the md_sim (the end of the Fig. 1 script's simulation
+ * object, Sec. 2), after waiting for its stream.  NULL is ignored.  A stream given to
+ * md_set_stream is not destroyed. */
 void md_destroy(md_sim *sim);
+/* Static text for an md_status code (the conventions above; unknown codes give a generic text).
+ * The paper has no error interface; this is the C counterpart of the Python exceptions the
+ * Fig. 1 script would see. */
 const char *md_strerror(int status);
+
+/* Measurement utility (the paper has no counterpart): the FP32 fused multiply-add throughput of
+ * the current GPU in TFLOP/s (2 flops per FMA), the denominator of the step kernel's FP32
+ * roofline.  Every SM is filled with independent FMA chains; the best of `repeats` >= 1 timed
+ * launches on cuda_stream (NULL = legacy default stream) is returned in *tflops, the SM count in
+ * *sms and that launch's duration in *ms (either may be NULL).  Allocates and frees a small
+ * device buffer.  MD_EINVAL for repeats < 1 or a NULL tflops, MD_ENOMEM, MD_ECUDA. */
+int md_measure_fp32_peak(void *cuda_stream, int repeats, double *tflops, int *sms, double *ms);
 
 /* Forces of one system for callers that cannot allocate device memory at call time.
  *
  * The paper has no counterpart: this entry point exists for callers that may not call
- * cudaMalloc when they need forces -- for instance a caller in the middle of capturing a CUDA
- * stream (allocation is not permitted there), a latency-critical loop that must never enter an
- * allocator, or a host framework that owns all device memory.  It needs no md_sim and allocates
- * nothing: inputs and outputs are the caller's device buffers, and the scratch it needs (the
- * particles sorted by cell) lives in one fixed array that every GPU loading this library reserves
- * (about 160 KB) and keeps until the process exits.
+ * cudaMalloc when they need forces -- a host framework that owns all device memory through its
+ * own pool and forbids libraries from allocating their own, or a latency-critical loop that must
+ * never enter the CUDA allocator (cudaMalloc / cudaFree can synchronise the device).  It needs no
+ * md_sim and allocates nothing: inputs and outputs are the caller's device buffers, and the
+ * scratch it needs (the particles sorted by cell) lives in one fixed array that every GPU loading
+ * this library reserves (about 160 KB) and keeps until the process exits.
  *
- *   pos   (n,3) FP64 device array, any periodic image;  type (n) int32 device array;
+ *   pos   (n,3) FP64 device array, any periodic image (folded into [0,L) on the device exactly
+ *         as md_set_state folds it);  type (n) int32 device array, every entry in [0,n_types)
+ *         (a particle with another type, and every particle within the stencil of one, gets NaN
+ *         outputs; nothing is read out of bounds);
  *   L     cubic box edge, > 2 rc_max;  params n_types x n_types HOST array (symmetric);
  *   f     (n,3) FP64 device output;  u, w (n) FP64 device outputs or NULL (u_i = 1/2 sum u_SP,
  *         w_i = 1/6 sum r.F);  uw: 2 FP64 device outputs (U, W) or NULL;

@@ -19,7 +19,7 @@
  *     distance is strictly below (rc_ab + s)^2 (Sec. 3 and Figs. 3-4), in FP64 and in a
  *     bit-defined FP32 arithmetic.
  *   - Optionally, a Coulomb term between charged particles cut off with the shifted-force method
- *     (Sec. 8 "Electrostatics": the molten-salt benchmark uses Coulomb forces with a large
+ *     (Sec. 9 "Electrostatics": the molten-salt benchmark uses Coulomb forces with a large
  *     shifted-force cutoff instead of a mesh/Ewald method).
  *   - A textbook linked-cell FP64 force routine (Sec. 6 cell-index method, cells of edge >= rc,
  *     27-cell stencil) used only for large-N baselines; it must equal the double loop.
@@ -29,7 +29,7 @@
  *   Shifted force (Sec. 2: "truncation plus shift of the pair force ... a linear term in the
  *   potential"): u_SF(r) = u(r) - u(rc) + (r - rc) F(rc), |F|_SF(r) = F(r) - F(rc), with
  *   F(r) = -u'(r), for r < rc.
- *   Coulomb, shifted force (charges q in units of sqrt(4 pi eps0 eps sigma), as Sec. 8 states):
+ *   Coulomb, shifted force (charges q in units of sqrt(4 pi eps0 eps sigma), as Sec. 9 states):
  *   u_C(r) = q_a q_b [1/r - 1/rc_C + (r - rc_C)/rc_C^2],  |F|_C(r) = q_a q_b [1/r^2 - 1/rc_C^2]
  *   for r < rc_C (the shifted-force construction above applied to u = q_a q_b / r); the LJ term
  *   keeps its own rc_ab.
@@ -100,7 +100,7 @@ static void lj_sp(double r2, double eps, double sig, double rc, double *u, doubl
     }
 }
 
-/* Coulomb shifted-force setting (Sec. 8): per-type charges and the Coulomb cutoff rc_C;
+/* Coulomb shifted-force setting (Sec. 9): per-type charges and the Coulomb cutoff rc_C;
  * rc_C <= 0 switches the term off (the default). */
 static double g_q[OR_MAX_TYPES];
 static double g_rcc = 0.0;

@@ -18,7 +18,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libmdgb300.so")
-SOURCES = ["md_kernels_f32.cu", "md_kernels_f64.cu", "md_runtime.cu", "md_static.cu"]
+SOURCES = ["md_kernels_f32.cu", "md_kernels_f64.cu", "md_runtime.cu", "md_static.cu",
+           "md_peak.cu"]
 HEADERS = ["md_internal.cuh", "md_kernels.cuh", "md_common.cuh", "md_step.cuh", "md_rebuild.cuh",
            "md_rep.cuh", "md_launch.inc"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -125,7 +125,7 @@ __device__ __forceinline__ void lj_pair(R dx, R dy, R dz, R r2, const C4 &c, con
     w += fs * r2;
 }
 
-// Shifted-force Coulomb term (Sec. 8, molten salt) for r < rc_C:
+// Shifted-force Coulomb term (Sec. 9, molten salt) for r < rc_C:
 // u = qq (1/r - 2/rc_C + r/rc_C^2), F_ij = (qq/r) (1/r^2 - 1/rc_C^2) r_ij.
 // q = {rc_C^2, qq, qq / rc_C^2, 2 qq / rc_C}.
 template <typename R, typename C4>

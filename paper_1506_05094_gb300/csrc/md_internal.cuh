@@ -57,7 +57,7 @@ struct PairTab {
     float fc, rc, padf[2];
     double rc2d, c12d, c6d, ushiftd, a12d, a6d, thr2d, padd;
     double fcd, rcd;
-    // shifted-force Coulomb (Sec. 8): rc_C^2, q_a q_b, q_a q_b / rc_C^2, 2 q_a q_b / rc_C
+    // shifted-force Coulomb (Sec. 9): rc_C^2, q_a q_b, q_a q_b / rc_C^2, 2 q_a q_b / rc_C
     float qrc2, qq, qf, qu;
     double qrc2d, qqd, qfd, qud;
 };

@@ -274,7 +274,8 @@ __global__ void __launch_bounds__(1024) k_rep(const StepArgs<R> a, const Rebuild
                                       px, py, pz, d2, st2);
             moved_any |= (int)moved;
             if (a.rebuild_batch > 1) disp_max_warp(s_disp, d2, st2);
-            R vals[MD_NRED] = {u * R(leader), w * R(leader), ke, px, py, pz};
+            double vals[MD_NRED] = {leader ? (double)u : 0.0, leader ? (double)w : 0.0,
+                                    (double)ke, (double)px, (double)py, (double)pz};
             // partials of tiles past the replica's last one are written to spare rows and ignored
             tile_partial(vals, s_tmp, s_part + (long long)t0 * MD_NRED, TT >> 5);
             __syncthreads();

@@ -59,7 +59,7 @@ struct md_sim {
     std::vector<SysDesc> sys;
     double mass[kMaxTypes], inv_mass[kMaxTypes];
     double skin = 0.3, rc_max = 0.0;
-    bool coul = false;                 // shifted-force Coulomb term on (Sec. 8)
+    bool coul = false;                 // shifted-force Coulomb term on (Sec. 9)
     double charge[kMaxTypes] = {};
     double rcc = 0.0;                  // Coulomb cutoff rc_C
     int integrator = MD_NVE_LEAPFROG;
@@ -95,6 +95,7 @@ struct md_sim {
     cudaGraph_t graph[2] = {nullptr, nullptr};
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
     int graph_len[2] = {0, 0};
+    long long graph_builds = 0;   // graphs captured and instantiated (md_stats)
     int sticky = MD_OK;
     long long overflows = 0;
     int device = 0;
@@ -491,6 +492,7 @@ int build_graph(md_sim *s, int p) {
         s->graph[p] = outg;
         s->exec[p] = exr;
         s->graph_len[p] = B;
+        s->graph_builds++;
         return MD_OK;
     }
     if (cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
@@ -567,6 +569,7 @@ int build_graph(md_sim *s, int p) {
     s->graph[p] = out;
     s->exec[p] = ex;
     s->graph_len[p] = B;
+    s->graph_builds++;
     return MD_OK;
 }
 
@@ -1425,6 +1428,7 @@ int md_get_stats(md_sim *s, md_stats *out) {
     out->graph_block = s->graph_block;
     out->n_total = s->ntot;
     out->neighbor_entries = ent;
+    out->graph_builds = s->graph_builds;
     return MD_OK;
 }
 

@@ -1,12 +1,13 @@
 // md_static.cu -- md_forces_static: forces of one system without allocating any device memory.
 //
-// Who needs this: code that may not call cudaMalloc at the moment it wants forces -- a caller
-// that is in the middle of capturing a CUDA stream (allocation is not permitted there), a
-// latency-critical loop that must never enter an allocator, or a host framework that owns all
-// device memory and forbids libraries from allocating their own.  Such a caller hands in device
-// buffers for the inputs and outputs; the scratch space this computation needs (positions
-// sorted by cell and their original indices) lives in one fixed array below, reserved when the
-// library is loaded on a device and held until the process exits.
+// Who needs this: code that may not call cudaMalloc at the moment it wants forces -- a host
+// framework that owns all device memory through its own pool and forbids libraries from
+// allocating behind its back (its memory budget is fixed up front), or a latency-critical loop
+// that must never enter the CUDA allocator (cudaMalloc and cudaFree can synchronise the device
+// and take far longer than the force evaluation itself).  Such a caller hands in device buffers
+// for the inputs and outputs; the scratch space this computation needs (positions sorted by cell
+// and their original indices) lives in one fixed array below, reserved when the library is
+// loaded on a device and held until the process exits.
 //
 // The computation is a one-CTA variant of the force evaluation: bin the particles into cells of
 // edge >= rc_max (27-cell stencil), sort them by cell into the scratch array, then sum the shifted-
@@ -40,6 +41,32 @@ struct StaticParams {
     float ush[kMaxTypes * kMaxTypes], a12[kMaxTypes * kMaxTypes], a6[kMaxTypes * kMaxTypes];
 };
 
+// Fold one coordinate into [0, L) with the steps of the host-side wrap in md_set_state: subtract
+// floor(v / L) periods, fold a result that rounded to L or below 0, and map L itself to 0.  Every
+// product and sum is rounded on its own (no contraction), so the counting pass and the scatter
+// pass, which both call this, bin every particle into the same cell.
+__device__ __forceinline__ double wrap_coord(double v, double L) {
+    v = __dsub_rn(v, __dmul_rn(L, floor(__ddiv_rn(v, L))));
+    if (v >= L) v = __dsub_rn(v, L);
+    if (v < 0.0) v = __dadd_rn(v, L);
+    if (v >= L) v = 0.0;   // -tiny + L rounded up to L
+    return v;
+}
+
+// Wrapped FP32 mirror of particle k (x, y, z, type bits) and its cell.
+__device__ __forceinline__ float4 wrapped_pos(const double *pos, const int *type, int k,
+                                              double Ld) {
+    const double x = wrap_coord(pos[3 * k], Ld), y = wrap_coord(pos[3 * k + 1], Ld),
+                 z = wrap_coord(pos[3 * k + 2], Ld);
+    return make_float4((float)x, (float)y, (float)z, __int_as_float(type[k]));
+}
+__device__ __forceinline__ int cell_of(const float4 &q, float cell_scale, int nc) {
+    const int cx = min(max(__float2int_rd(q.x * cell_scale), 0), nc - 1);
+    const int cy = min(max(__float2int_rd(q.y * cell_scale), 0), nc - 1);
+    const int cz = min(max(__float2int_rd(q.z * cell_scale), 0), nc - 1);
+    return (cz * nc + cy) * nc + cx;
+}
+
 __device__ __forceinline__ float mi(float xi, float xj, float xa, float nfl, float half, float L) {
     // minimum image with the coordinate near L shifted first (exact), as in the main path
     const float t = __fsub_rn(xi, xj);
@@ -62,14 +89,8 @@ __global__ void __launch_bounds__(kThreads) k_forces_static(StaticParams p, void
     // 1. cell counts start at zero on every call (the previous call left its own)
     for (int c = threadIdx.x; c < C; c += blockDim.x) s_cnt[c] = 0;
     __syncthreads();
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        double x = pos[3 * k], y = pos[3 * k + 1], z = pos[3 * k + 2];
-        x -= p.Ld * floor(x / p.Ld); y -= p.Ld * floor(y / p.Ld); z -= p.Ld * floor(z / p.Ld);
-        const int cx = min(max(__float2int_rd((float)x * p.cell_scale), 0), nc - 1);
-        const int cy = min(max(__float2int_rd((float)y * p.cell_scale), 0), nc - 1);
-        const int cz = min(max(__float2int_rd((float)z * p.cell_scale), 0), nc - 1);
-        atomicAdd(s_cnt + (cz * nc + cy) * nc + cx, 1);
-    }
+    for (int k = threadIdx.x; k < n; k += blockDim.x)
+        atomicAdd(s_cnt + cell_of(wrapped_pos(pos, type, k, p.Ld), p.cell_scale, nc), 1);
     __syncthreads();
     // 2. exclusive scan of the counts (one chunk of cells per thread)
     {
@@ -105,17 +126,10 @@ __global__ void __launch_bounds__(kThreads) k_forces_static(StaticParams p, void
     }
     __syncthreads();
     // 3. scatter positions (FP32 mirror of the wrapped FP64 input) and indices into the scratch
+    //    (the same wrap and cell as the counting pass, so every cell's slots are filled exactly)
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        double x = pos[3 * k], y = pos[3 * k + 1], z = pos[3 * k + 2];
-        x -= p.Ld * floor(x / p.Ld); y -= p.Ld * floor(y / p.Ld); z -= p.Ld * floor(z / p.Ld);
-        if (x >= p.Ld) x = 0.0;
-        if (y >= p.Ld) y = 0.0;
-        if (z >= p.Ld) z = 0.0;
-        const float4 q = make_float4((float)x, (float)y, (float)z, __int_as_float(type[k]));
-        const int cx = min(max(__float2int_rd(q.x * p.cell_scale), 0), nc - 1);
-        const int cy = min(max(__float2int_rd(q.y * p.cell_scale), 0), nc - 1);
-        const int cz = min(max(__float2int_rd(q.z * p.cell_scale), 0), nc - 1);
-        const int slot = atomicAdd(s_cnt + (cz * nc + cy) * nc + cx, 1);
+        const float4 q = wrapped_pos(pos, type, k, p.Ld);
+        const int slot = atomicAdd(s_cnt + cell_of(q, p.cell_scale, nc), 1);
         spos[slot] = q;
         sidx[slot] = k;
     }
@@ -126,14 +140,16 @@ __global__ void __launch_bounds__(kThreads) k_forces_static(StaticParams p, void
     for (int s = threadIdx.x; s < n; s += blockDim.x) {
         const float4 ri = spos[s];
         const int ti = __float_as_int(ri.w);
+        // a type outside [0, n_types) would index past the coefficient tables: such a particle,
+        // and every particle that meets one in its stencil, gets NaN outputs instead
+        bool bad = (unsigned)ti >= (unsigned)p.nt;
         const bool ux = ri.x >= p.halfL, uy = ri.y >= p.halfL, uz = ri.z >= p.halfL;
         const float xa = ux ? __fsub_rn(__fsub_rn(ri.x, p.L), p.Llo) : __fadd_rn(ri.x, p.Llo);
         const float ya = uy ? __fsub_rn(__fsub_rn(ri.y, p.L), p.Llo) : __fadd_rn(ri.y, p.Llo);
         const float za = uz ? __fsub_rn(__fsub_rn(ri.z, p.L), p.Llo) : __fadd_rn(ri.z, p.Llo);
         const float nx = ux ? 0.f : 1.f, ny = uy ? 0.f : 1.f, nz = uz ? 0.f : 1.f;
-        const int cx = min(max(__float2int_rd(ri.x * p.cell_scale), 0), nc - 1);
-        const int cy = min(max(__float2int_rd(ri.y * p.cell_scale), 0), nc - 1);
-        const int cz = min(max(__float2int_rd(ri.z * p.cell_scale), 0), nc - 1);
+        const int ci = cell_of(ri, p.cell_scale, nc);
+        const int cx = ci % nc, cy = (ci / nc) % nc, cz = ci / (nc * nc);
         float fx = 0.f, fy = 0.f, fz = 0.f, uu = 0.f, ww = 0.f;
         for (int oz = 0; oz < span; ++oz) {
             const int zz = span == nc ? oz : (cz - 1 + oz + nc) % nc;
@@ -142,9 +158,13 @@ __global__ void __launch_bounds__(kThreads) k_forces_static(StaticParams p, void
                 for (int ox = 0; ox < span; ++ox) {
                     const int xx = span == nc ? ox : (cx - 1 + ox + nc) % nc;
                     const int c = (zz * nc + yy) * nc + xx;
-                    for (int j = s_start[c]; j < s_start[c + 1]; ++j) {
+                    for (int j = s_start[c]; j < s_start[c + 1] && !bad; ++j) {
                         if (j == s) continue;
                         const float4 rj = spos[j];
+                        if ((unsigned)__float_as_int(rj.w) >= (unsigned)p.nt) {
+                            bad = true;
+                            break;
+                        }
                         const float dx = mi(ri.x, rj.x, xa, nx, p.halfL, p.L);
                         const float dy = mi(ri.y, rj.y, ya, ny, p.halfL, p.L);
                         const float dz = mi(ri.z, rj.z, za, nz, p.halfL, p.L);
@@ -162,6 +182,7 @@ __global__ void __launch_bounds__(kThreads) k_forces_static(StaticParams p, void
             }
         }
         const int k = sidx[s];
+        if (bad) fx = fy = fz = uu = ww = __int_as_float(0x7fc00000);   // NaN
         f[3 * k] = fx; f[3 * k + 1] = fy; f[3 * k + 2] = fz;
         const float ui = 0.5f * uu, wi = ww * (1.0f / 6.0f);
         if (u) u[k] = ui;

@@ -194,12 +194,12 @@ __device__ __forceinline__ int rebuild_needed(const StepArgs<R> &a, long long ne
     return (sqrtf(d2max) + grow > a.half_skin) ? 1 : 0;
 }
 
-// Sum of one tile's per-particle values: within a warp in R, across the tile's warps in FP64 in
-// warp order; a tile is `tw` consecutive warps of the block (tw = blockDim/32 in the grid kernel).
-// Thread (k, q), k < tiles in the block, writes quantity q of tile k to out[k * MD_NRED + q].
-// Call with the whole block.
-template <typename R>
-__device__ __forceinline__ void tile_partial(R vals[MD_NRED], double (*s_tmp)[MD_NRED],
+// Sum of one tile's per-particle values, all in FP64 (each particle's u_i, w_i, kinetic energy
+// and momentum are converted to double before the first addition): within a warp by a fixed
+// shuffle tree, across the tile's warps in warp order; a tile is `tw` consecutive warps of the
+// block (tw = blockDim/32 in the grid kernel).  Thread (k, q), k < tiles in the block, writes
+// quantity q of tile k to out[k * MD_NRED + q].  Call with the whole block.
+__device__ __forceinline__ void tile_partial(double vals[MD_NRED], double (*s_tmp)[MD_NRED],
                                              double *out, int tw) {
 #pragma unroll
     for (int q2 = 0; q2 < MD_NRED; ++q2)
@@ -208,7 +208,7 @@ __device__ __forceinline__ void tile_partial(R vals[MD_NRED], double (*s_tmp)[MD
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (lane == 0)
 #pragma unroll
-        for (int q2 = 0; q2 < MD_NRED; ++q2) s_tmp[warp][q2] = (double)vals[q2];
+        for (int q2 = 0; q2 < MD_NRED; ++q2) s_tmp[warp][q2] = vals[q2];
     __syncthreads();
     const int ntile = nw / tw;
     if (threadIdx.x < ntile * MD_NRED) {
@@ -410,7 +410,8 @@ __global__ void __launch_bounds__(1024) k_step(const StepArgs<R> a) {
     if (__ballot_sync(FULL_MASK, moved) != 0u && (threadIdx.x & 31) == 0) atomicOr(a.moved + r, 1);
     if (a.rebuild_batch > 1) disp_max_warp(a.disp + 2 * r, d2, st2);
 
-    R vals[MD_NRED] = {u * R(leader), w * R(leader), ke, px, py, pz};
+    double vals[MD_NRED] = {leader ? (double)u : 0.0, leader ? (double)w : 0.0, (double)ke,
+                            (double)px, (double)py, (double)pz};
     tile_partial(vals, s_tmp, a.partial + (long long)tile * MD_NRED, blockDim.x >> 5);
     __threadfence();
     __syncthreads();

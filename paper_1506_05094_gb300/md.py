@@ -31,7 +31,7 @@ SYMBOLS = ("md_create", "md_set_integrator", "md_set_state", "md_set_stream", "m
            "md_set_graph_block", "md_autotune",
            "md_get_stats", "md_profile", "md_set_log", "md_get_log", "md_checkpoint_size",
            "md_save_checkpoint", "md_load_checkpoint", "md_destroy", "md_strerror",
-           "md_forces_static")
+           "md_forces_static", "md_measure_fp32_peak")
 
 
 class md_pair(C.Structure):
@@ -56,7 +56,8 @@ class md_stats(C.Structure):
                 ("rebuild_kernels", C.c_int),
                 ("step_kernels", C.c_int),
                 ("graph_block", C.c_int),
-                ("n_total", C.c_longlong), ("neighbor_entries", C.c_longlong)]
+                ("n_total", C.c_longlong), ("neighbor_entries", C.c_longlong),
+                ("graph_builds", C.c_longlong)]
 
 
 class md_timing(C.Structure):
@@ -118,6 +119,7 @@ def lib():
         "md_destroy": [p],
         "md_strerror": [i],
         "md_forces_static": [p, p, i, d, i, C.POINTER(md_pair), p, p, p, p, p],
+        "md_measure_fp32_peak": [p, i, pd, pi, pd],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -376,3 +378,13 @@ class Sim:
     def load_checkpoint(self, blob: bytes):
         buf = (C.c_ubyte * len(blob)).from_buffer_copy(blob)
         _ck(lib().md_load_checkpoint(self._h, buf, len(blob)), "md_load_checkpoint")
+
+
+def measure_fp32_peak(stream_handle=None, repeats: int = 5) -> dict:
+    """FP32 FMA throughput of the current GPU (md_measure_fp32_peak): TFLOP/s, SMs, ms."""
+    tf, ms = C.c_double(), C.c_double()
+    sms = C.c_int()
+    _ck(lib().md_measure_fp32_peak(C.c_void_p(int(stream_handle or 0)), int(repeats),
+                                   C.byref(tf), C.byref(sms), C.byref(ms)),
+        "md_measure_fp32_peak")
+    return {"tflops": tf.value, "sms": sms.value, "ms": ms.value}

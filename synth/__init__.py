@@ -244,7 +244,7 @@ class Workload:
 
 
 def workload(name: str, replicas: int | None = None) -> Workload:
-    """Recipes.  Names: lj1000, ka8000, lj131072, ka_ensemble512, ka_ensemble64, and the
+    """Recipes.  Names: lj1000, ka8000, lj131072, lj1048576, ka_ensemble512, ka_ensemble64, and the
     Coulomb (molten salt) systems salt2000, salt20000, salt100000.
 
     ``replicas`` trims a batched recipe to its first R replicas (same seeds), for small tests.
@@ -261,6 +261,11 @@ def workload(name: str, replicas: int | None = None) -> Workload:
     if name == "lj131072":
         m = lj_model()
         return Workload(name, m, [lj_fcc_state(131072, 0.8442, 0.72, 1003, m)], "nve", 0.005,
+                        0.72, tau, skin, 100)
+    if name == "lj1048576":
+        # the same melting-fcc recipe at 4 * 64^3 particles: a working set well beyond the L2
+        m = lj_model()
+        return Workload(name, m, [lj_fcc_state(1048576, 0.8442, 0.72, 1007, m)], "nve", 0.005,
                         0.72, tau, skin, 100)
     if name in ("ka_ensemble512", "ka_ensemble64"):
         if name == "ka_ensemble512":

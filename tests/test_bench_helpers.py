@@ -44,9 +44,51 @@ def test_fp32_peak_from_unit_counts():
     assert bench.fp32_peak_tflops(2070.0, 152) == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
 
 
-@pytest.mark.parametrize("steps,block", [(2000, 100), (1000, 100), (1001, 200), (7, 6), (2, 2)])
+@pytest.mark.parametrize("steps,block", [(2000, 100), (1000, 100), (20, 4), (200, 40),
+                                         (1001, 100), (7, 6), (2, 2)])
 def test_pick_block(steps, block):
+    """The largest even block <= 100 that cuts the run into 5 equal segments of whole graphs,
+    else the largest even divisor <= 100 (an odd count keeps one plain step)."""
     assert bench.pick_block(steps) == block
+
+
+class _FakeSim:
+    """Counts graph builds the way md_step does: one per (parity, block) not yet captured."""
+
+    def __init__(self):
+        self.step_no, self.gb, self.graphs, self.builds = 5, 0, set(), 0
+
+    def set_graph_block(self, gb):
+        if gb != self.gb:
+            self.graphs.clear()
+        self.gb = gb
+
+    def step(self, n):
+        while n > 0:
+            if self.gb and n >= self.gb:
+                key = self.step_no & 1
+                if key not in self.graphs:
+                    self.graphs.add(key)
+                    self.builds += 1
+                self.step_no += self.gb
+                n -= self.gb
+            else:
+                self.step_no += 1
+                n -= 1
+
+    def stats(self):
+        return {"graph_builds": self.builds}
+
+
+@pytest.mark.parametrize("gb,warmup,steps", [(4, 5, 20), (100, 10, 2000), (1, 3, 200)])
+def test_prepare_graphs_leaves_no_build_for_the_timed_region(gb, warmup, steps):
+    sim = _FakeSim()
+    bench.prepare_graphs(sim, gb)
+    assert sim.graphs == {0, 1}
+    sim.step(warmup)
+    before = sim.stats()["graph_builds"]
+    sim.step(steps)
+    assert sim.stats()["graph_builds"] == before
 
 
 def test_clock_log_parsing():

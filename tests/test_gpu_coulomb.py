@@ -1,4 +1,4 @@
-"""GPU parity of the shifted-force Coulomb term (Sec. 8 molten salt: charged LJ particles, charges
+"""GPU parity of the shifted-force Coulomb term (Sec. 9 molten salt: charged LJ particles, charges
 +-1, rho = 0.3677, T = 2, dt = 0.004, Coulomb cut at 6.0) against the FP64 oracle.
 
 Tolerances are those of test_gpu_parity.py (forces 1e-5 relative RMS, U 1e-6 relative, pair sets

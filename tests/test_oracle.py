@@ -324,7 +324,7 @@ def test_shifted_force_gradient_and_virial():
 
 
 # --------------------------------------------------------------------------------------------
-# Coulomb with the shifted-force cutoff (Sec. 8, molten-salt benchmark)
+# Coulomb with the shifted-force cutoff (Sec. 9, molten-salt benchmark)
 # --------------------------------------------------------------------------------------------
 
 SALT = synth.salt_model()
