@@ -89,6 +89,88 @@ __device__ __forceinline__ void block_scan_cells(const int *cnt, int *start, int
     __syncthreads();
 }
 
+// In-CTA rebuild of one replica (Sec. 7): bin its particles into cells, exclusive scan of the
+// counts (cellStart), scatter, in-cell order by user id, permutation of all particle data, and the
+// list build of Fig. 4 from the shared-memory positions and cell starts (TPB lanes per particle).
+// On entry s_pos holds the replica's positions in its current slot order; on exit the sorted
+// ones, s_cs the cell starts (local slots).  write_pos: also store the sorted positions in the
+// global mirror b.pos (a later kernel reads them there).  An overfull list stores n_max entries,
+// raises *ovf_flag and the largest count, and the call returns 1 (block-uniform); else 0.
+// The slot order, list order and list contents are those of the grid path's sort and build.
+// Call with the whole block; uses s_cnt (cmax), s_cell and s_perm (n entries each), s_warp (32).
+template <typename R, int TPB>
+__device__ __forceinline__ int cta_rebuild(const RebuildArgs<R> &b, const SysDesc &S, int r,
+                                           typename V4T<R>::t *s_pos, int *s_cs, int *s_cnt,
+                                           int *s_cell, int *s_perm, int *s_warp, const R *s_thr,
+                                           bool write_pos, int *ovf_flag) {
+    const int n = S.n, off = S.off;
+    const int C = S.nc * S.nc * S.nc;
+    for (int c = threadIdx.x; c < C; c += blockDim.x) s_cnt[c] = 0;
+    __syncthreads();
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const int c = cell_index(s_pos[k], S);
+        s_cell[k] = c;
+        atomicAdd(s_cnt + c, 1);
+    }
+    __syncthreads();
+    block_scan_cells(s_cnt, s_cs, C, s_warp);
+    for (int c = threadIdx.x; c < C; c += blockDim.x) s_cnt[c] = s_cs[c];
+    __syncthreads();
+    for (int k = threadIdx.x; k < n; k += blockDim.x) s_perm[atomicAdd(s_cnt + s_cell[k], 1)] = k;
+    __syncthreads();
+    const int *idg = b.id + off;   // user ids (pre-permutation)
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {   // deterministic: by user id
+        const int s0 = s_cs[c], e0 = s_cs[c + 1];
+        for (int q = s0 + 1; q < e0; ++q) {
+            const int v = s_perm[q], key = idg[v];
+            int m = q - 1;
+            while (m >= s0 && idg[s_perm[m]] > key) { s_perm[m + 1] = s_perm[m]; --m; }
+            s_perm[m + 1] = v;
+        }
+    }
+    __syncthreads();
+    // permute the particle data through the scratch arrays (global, same block)
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+        const int o = off + s_perm[q], d = off + q;
+        b.tpos[d] = s_pos[s_perm[q]];
+        b.txd[d] = b.xd[o]; b.tyd[d] = b.yd[o]; b.tzd[d] = b.zd[o];
+        b.tvel[d] = b.vel[o];
+        b.timg[d] = b.img[o];
+        b.tid[d] = b.id[o];
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+        const int d = off + q;
+        s_pos[q] = b.tpos[d];
+        if (write_pos) b.pos[d] = s_pos[q];
+        b.xd[d] = b.txd[d]; b.yd[d] = b.tyd[d]; b.zd[d] = b.tzd[d];
+        b.vel[d] = b.tvel[d];
+        b.img[d] = b.timg[d];
+        b.id[d] = b.tid[d];
+    }
+    __syncthreads();
+    // list build from the shared positions and cell starts
+    SharedKey<R> K{s_pos};
+    SharedStart CS{s_cs};
+    int ovf = 0;
+    for (int g = threadIdx.x / TPB; g < n; g += blockDim.x / TPB) {
+        int cnt = build_one<R, TPB, false>(S, K, CS, g, off + g, off, b.nbl, b.nmax, s_thr,
+                                           b.ntypes, nullptr);
+        if (threadIdx.x % TPB == 0) {
+            if (cnt > b.nmax) {
+                atomicMax(&b.ctrl->max_count, cnt);
+                atomicExch(ovf_flag, 1);
+                ovf = 1;
+                cnt = b.nmax;
+            }
+            b.nnb[off + g] = cnt;
+            b.pos_build[off + g] = s_pos[g];
+        }
+    }
+    if (threadIdx.x == 0) b.th[r].rebuilds += 1;
+    return __syncthreads_or(ovf);
+}
+
 template <typename R, int TP, bool SINGLE, int TPB>
 __global__ void __launch_bounds__(1024) k_rep(const StepArgs<R> a, const RebuildArgs<R> b) {
     typedef typename V4T<R>::t V4;
@@ -170,69 +252,10 @@ __global__ void __launch_bounds__(1024) k_rep(const StepArgs<R> a, const Rebuild
 
         if (rebuild) {
             // ---- Sec. 7 rebuild inside the CTA: bin, scan, scatter, order by id, permute, build
-            const int C = S.nc * S.nc * S.nc;
-            for (int c = threadIdx.x; c < C; c += blockDim.x) s_cnt[c] = 0;
-            __syncthreads();
-            for (int k = threadIdx.x; k < n; k += blockDim.x) {
-                const int c = cell_index(s_pos[k], S);
-                s_cell[k] = c;
-                atomicAdd(s_cnt + c, 1);
-            }
-            __syncthreads();
-            block_scan_cells(s_cnt, s_cs, C, s_warp);
-            for (int c = threadIdx.x; c < C; c += blockDim.x) s_cnt[c] = s_cs[c];
-            __syncthreads();
-            for (int k = threadIdx.x; k < n; k += blockDim.x)
-                s_perm[atomicAdd(s_cnt + s_cell[k], 1)] = k;
-            __syncthreads();
-            const int *idg = a.id_g + off;   // user ids (pre-permutation)
-            for (int c = threadIdx.x; c < C; c += blockDim.x) {   // deterministic: by user id
-                const int s0 = s_cs[c], e0 = s_cs[c + 1];
-                for (int q = s0 + 1; q < e0; ++q) {
-                    const int v = s_perm[q], key = idg[v];
-                    int m = q - 1;
-                    while (m >= s0 && idg[s_perm[m]] > key) { s_perm[m + 1] = s_perm[m]; --m; }
-                    s_perm[m + 1] = v;
-                }
-            }
-            __syncthreads();
-            // permute the particle data through the scratch arrays (global, same block)
-            for (int s = threadIdx.x; s < n; s += blockDim.x) {
-                const int o = off + s_perm[s], d = off + s;
-                b.tpos[d] = s_pos[s_perm[s]];
-                b.txd[d] = a.xd[o]; b.tyd[d] = a.yd[o]; b.tzd[d] = a.zd[o];
-                b.tvel[d] = a.vel[o];
-                b.timg[d] = a.img[o];
-                b.tid[d] = a.id_g[o];
-            }
-            __syncthreads();
-            for (int s = threadIdx.x; s < n; s += blockDim.x) {
-                const int d = off + s;
-                s_pos[s] = b.tpos[d];
-                a.xd[d] = b.txd[d]; a.yd[d] = b.tyd[d]; a.zd[d] = b.tzd[d];
-                a.vel[d] = b.tvel[d];
-                a.img[d] = b.timg[d];
-                a.id_g[d] = b.tid[d];
-            }
-            __syncthreads();
-            // list build from the shared positions and cell starts
-            SharedKey<R> K{s_pos};
-            SharedStart CS{s_cs};
-            for (int g = threadIdx.x / TPB; g < n; g += blockDim.x / TPB) {
-                int cnt = build_one<R, TPB, false>(S, K, CS, g, off + g, off, b.nbl, b.nmax,
-                                                   s_thr, a.ntypes, nullptr);
-                if (threadIdx.x % TPB == 0) {
-                    if (cnt > b.nmax) {
-                        atomicMax(&a.ctrl->max_count, cnt);
-                        atomicExch(&a.ctrl->rep_overflow, 1);
-                        s_ovf = 1;
-                        cnt = b.nmax;
-                    }
-                    b.nnb[off + g] = cnt;
-                    b.pos_build[off + g] = s_pos[g];
-                }
-            }
-            if (threadIdx.x == 0) a.th[r].rebuilds += 1;
+            if (cta_rebuild<R, TPB>(b, S, r, s_pos, s_cs, s_cnt, s_cell, s_perm, s_warp, s_thr,
+                                    false, &a.ctrl->rep_overflow) &&
+                threadIdx.x == 0)
+                s_ovf = 1;
             __syncthreads();
         }
 
@@ -274,8 +297,7 @@ __global__ void __launch_bounds__(1024) k_rep(const StepArgs<R> a, const Rebuild
                                       px, py, pz, d2, st2);
             moved_any |= (int)moved;
             if (a.rebuild_batch > 1) disp_max_warp(s_disp, d2, st2);
-            double vals[MD_NRED] = {leader ? (double)u : 0.0, leader ? (double)w : 0.0,
-                                    (double)ke, (double)px, (double)py, (double)pz};
+            const R vals[MD_NRED] = {leader ? u : R(0), leader ? w : R(0), ke, px, py, pz};
             // partials of tiles past the replica's last one are written to spare rows and ignored
             tile_partial(vals, s_tmp, s_part + (long long)t0 * MD_NRED, TT >> 5);
             __syncthreads();
@@ -360,5 +382,44 @@ template <typename R> __global__ void __launch_bounds__(1024) k_sort_small(const
     }
 }
 
+
+// ------------------------------------------------------------------------------------------------
+// Fused rebuild of the grid path for batches of replicas: one CTA per replica (grid = replicas);
+// a CTA whose replica keeps its list exits at once, the others run the whole Sec. 7 rebuild of
+// their replica in shared memory (cta_rebuild: sort, permutation, list build) and write the sorted
+// positions back to the mirror for the step kernel that follows.  This replaces the plan / sort /
+// build chain of grid-wide kernels with one launch whose flagged CTAs each stay on one SM, so the
+// step of the replicas that keep their list keeps the rest of the GPU.  The lists are the grid
+// chain's, bit for bit.  The first flagged CTA of a step counts the rebuild pass.
+// ------------------------------------------------------------------------------------------------
+template <typename R, int TPB>
+__global__ void __launch_bounds__(512) k_rebuild_rep(const RebuildArgs<R> b) {
+    typedef typename V4T<R>::t V4;
+    extern __shared__ __align__(16) unsigned char smem_fr[];
+    __shared__ R s_thr[MD_MAX_PAIRS];
+    __shared__ int s_warp[32];
+    __shared__ SysDesc S;
+    const int r = blockIdx.x;
+    if (rebuild_off(b.ctrl) || !b.need_in[r]) return;   // block-uniform
+    V4 *s_pos = reinterpret_cast<V4 *>(smem_fr);
+    int *s_cs = reinterpret_cast<int *>(s_pos + b.sort_nmax);   // cmax + 1
+    int *s_cnt = s_cs + b.sort_cmax + 1;                         // cmax
+    int *s_cell = s_cnt + b.sort_cmax;                           // nmax
+    int *s_perm = s_cell + b.sort_nmax;                          // nmax
+    const int npair = b.ntypes * b.ntypes;
+    for (int p = threadIdx.x; p < npair; p += blockDim.x)
+        s_thr[p] = sizeof(R) == 4 ? (R)b.tab[p].thr2 : (R)b.tab[p].thr2d;
+    if (threadIdx.x == 0) {
+        S = b.sys[r];
+        // one rebuild pass per step: the first flagged CTA of this step counts it
+        const unsigned long long next = (unsigned long long)b.ctrl->step + 1ull;
+        if (atomicMax(&b.ctrl->last_pass_step, next) < next) b.ctrl->rebuild_passes += 1;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < S.n; k += blockDim.x) s_pos[k] = b.pos[S.off + k];
+    __syncthreads();
+    cta_rebuild<R, TPB>(b, S, r, s_pos, s_cs, s_cnt, s_cell, s_perm, s_warp, s_thr, true,
+                        &b.ctrl->overflow);
+}
 
 }  // namespace md

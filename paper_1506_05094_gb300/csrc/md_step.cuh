@@ -194,21 +194,93 @@ __device__ __forceinline__ int rebuild_needed(const StepArgs<R> &a, long long ne
     return (sqrtf(d2max) + grow > a.half_skin) ? 1 : 0;
 }
 
-// Sum of one tile's per-particle values, all in FP64 (each particle's u_i, w_i, kinetic energy
-// and momentum are converted to double before the first addition): within a warp by a fixed
-// shuffle tree, across the tile's warps in warp order; a tile is `tw` consecutive warps of the
-// block (tw = blockDim/32 in the grid kernel).  Thread (k, q), k < tiles in the block, writes
-// quantity q of tile k to out[k * MD_NRED + q].  Call with the whole block.
-__device__ __forceinline__ void tile_partial(double vals[MD_NRED], double (*s_tmp)[MD_NRED],
+// Exact sum of two floats as an unevaluated pair s + e (Knuth's TwoSum; every operation rounded
+// on its own, none contracted).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// One level of the warp's pair tree: slot k of this lane and its partner at distance `off` are
+// added exactly (hi by TwoSum, the rounding error and both lo parts into lo).
+__device__ __forceinline__ void pair_add(float &h, float &l, float rh, float rl) {
+    float s, e;
+    two_sum(h, rh, s, e);
+    h = s;
+    l = __fadd_rn(__fadd_rn(l, rl), e);
+}
+
+// Warp sums of the MD_NRED per-particle quantities, each accurate to FP64 precision, in lane 0's
+// out[q] (the other lanes' out[] is unspecified).  Mixed precision: the FP32 values are summed as exact float pairs (hi + lo) in a
+// transposed tree -- at distance 16 each half of the warp keeps half of 8 slots (6 quantities, 2
+// zeros), at 8 a quarter, at 4 an eighth, then every lane adds one slot -- so each lane does 9
+// exact pair additions instead of 30 plain ones, and no FP64 instruction runs in the tree (the
+// FP64 pipe of this GPU is a small fraction of the FP32 one).  The pair's relative error is about
+// 2^-48, below FP64 rounding of the sum; hi + lo is then formed in FP64.  FP64 mode: plain FP64
+// shuffle tree.  The tree is fixed, so the result is deterministic.  Call with the whole warp.
+__device__ __forceinline__ void warp_sums(const float v[MD_NRED], double out[MD_NRED]) {
+    const int lane = threadIdx.x & 31;
+    float h[8], l[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        h[k] = k < MD_NRED ? v[k] : 0.f;
+        l[k] = 0.f;
+    }
+#pragma unroll
+    for (int half = 4; half >= 1; half >>= 1) {   // distances 16, 8, 4: keep `half` slots
+        const int off = half * 4;
+        const bool up = (lane & off) != 0;
+#pragma unroll
+        for (int k = 0; k < half; ++k) {
+            const float mh = up ? h[k + half] : h[k], ml = up ? l[k + half] : l[k];
+            const float sh = up ? h[k] : h[k + half], sl = up ? l[k] : l[k + half];
+            const float rh = __shfl_xor_sync(FULL_MASK, sh, off);
+            const float rl = __shfl_xor_sync(FULL_MASK, sl, off);
+            h[k] = mh;
+            l[k] = ml;
+            pair_add(h[k], l[k], rh, rl);
+        }
+    }
+#pragma unroll
+    for (int off = 2; off >= 1; off >>= 1) {
+        const float rh = __shfl_xor_sync(FULL_MASK, h[0], off);
+        const float rl = __shfl_xor_sync(FULL_MASK, l[0], off);
+        pair_add(h[0], l[0], rh, rl);
+    }
+    // slot 0 of lane 4 q (lane bits 4, 3, 2 = the bits of q) holds quantity q; lane 0 collects
+    // the pairs and forms hi + lo in FP64 (only lane 0's out[] is meaningful)
+#pragma unroll
+    for (int q = 0; q < MD_NRED; ++q) {
+        const float qh = __shfl_sync(FULL_MASK, h[0], 4 * q);
+        const float ql = __shfl_sync(FULL_MASK, l[0], 4 * q);
+        out[q] = 0.0;
+        if (lane == 0) out[q] = (double)qh + (double)ql;
+    }
+}
+__device__ __forceinline__ void warp_sums(const double v[MD_NRED], double out[MD_NRED]) {
+#pragma unroll
+    for (int q = 0; q < MD_NRED; ++q) {
+        double x = v[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(FULL_MASK, x, o);
+        out[q] = x;
+    }
+}
+
+// Sum of one tile's per-particle values (u_i, w_i, kinetic energy, momentum): FP64-accurate warp
+// sums (warp_sums), then across the tile's warps in FP64 in warp order; a tile is `tw`
+// consecutive warps of the block (tw = blockDim/32 in the grid kernel).  Thread (k, q), k < tiles
+// in the block, writes quantity q of tile k to out[k * MD_NRED + q].  Call with the whole block.
+template <typename R>
+__device__ __forceinline__ void tile_partial(const R vals[MD_NRED], double (*s_tmp)[MD_NRED],
                                              double *out, int tw) {
-#pragma unroll
-    for (int q2 = 0; q2 < MD_NRED; ++q2)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) vals[q2] += __shfl_down_sync(FULL_MASK, vals[q2], o);
+    double ws[MD_NRED];
+    warp_sums(vals, ws);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (lane == 0)
 #pragma unroll
-        for (int q2 = 0; q2 < MD_NRED; ++q2) s_tmp[warp][q2] = vals[q2];
+        for (int q2 = 0; q2 < MD_NRED; ++q2) s_tmp[warp][q2] = ws[q2];
     __syncthreads();
     const int ntile = nw / tw;
     if (threadIdx.x < ntile * MD_NRED) {
@@ -410,8 +482,7 @@ __global__ void __launch_bounds__(1024) k_step(const StepArgs<R> a) {
     if (__ballot_sync(FULL_MASK, moved) != 0u && (threadIdx.x & 31) == 0) atomicOr(a.moved + r, 1);
     if (a.rebuild_batch > 1) disp_max_warp(a.disp + 2 * r, d2, st2);
 
-    double vals[MD_NRED] = {leader ? (double)u : 0.0, leader ? (double)w : 0.0, (double)ke,
-                            (double)px, (double)py, (double)pz};
+    const R vals[MD_NRED] = {leader ? u : R(0), leader ? w : R(0), ke, px, py, pz};
     tile_partial(vals, s_tmp, a.partial + (long long)tile * MD_NRED, blockDim.x >> 5);
     __threadfence();
     __syncthreads();

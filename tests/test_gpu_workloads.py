@@ -117,7 +117,9 @@ def test_ka_ensemble64_nve_1e6_steps_per_replica_drift():
       - over the same 1e5-step window, that replica's GPU drift equals the oracle's within the
         two fits' combined standard error x 5 plus 2e-7 (the resolution of a slope over 250 time
         units of E/N samples);
-      - over the 1e6 steps every replica's drift is below 2e-6 per particle per unit time.
+      - over the 1e6 steps every replica's drift is below 1e-5 per particle per unit time, about
+        2.5x the FP64 oracle's own drift over its 1e5-step window (4.1e-6 +- 2.0e-6 measured: the
+        shifted potential's force jump at rc does not conserve energy exactly in any precision).
     """
     import threading
 
@@ -164,4 +166,4 @@ def test_ka_ensemble64_nve_1e6_steps_per_replica_drift():
     print(f"ka_ensemble64 replica {k} (N={st.n}), first 1e5 steps: GPU drift {d_win:.3e} "
           f"+- {se_win:.1e}, FP64 oracle drift {d_or:.3e} +- {se_or:.1e}")
     assert abs(d_win - d_or) <= 5 * np.hypot(se_win, se_or) + 2e-7
-    assert np.abs(d_all).max() < 2e-6
+    assert np.abs(d_all).max() < 1e-5
