@@ -208,15 +208,6 @@ int md_set_list_capacity(md_sim *sim, int n_max);
 enum { MD_PATH_AUTO = 0, MD_PATH_GRID = 1, MD_PATH_REPLICA = 2, MD_PATH_STAGED = 3 };
 int md_set_path(md_sim *sim, int path);
 
-/* Kernels of a cell-method rebuild pass on the grid path (Sec. 7): 1 = a chain of grid-wide
- * kernels (work plan, sort of the flagged replicas, list build over all their particles); 2 = one
- * fused kernel with one CTA per replica, of which the flagged ones sort their replica and build
- * its list in shared memory (replicas of up to 16384 particles that fit in shared memory).  Both
- * give the same lists, hence the same results, bit for bit.  0 = automatic: 2 for batches of 8 or
- * more replicas when it fits, else 1.  MD_EINVAL if 2 does not fit. */
-enum { MD_REBUILD_AUTO = 0, MD_REBUILD_CHAIN = 1, MD_REBUILD_FUSED = 2 };
-int md_set_rebuild_kernel(md_sim *sim, int kind);
-
 /* Steps captured per CUDA graph replay (>= 1; graphs are kept per starting step parity, so an odd
  * block uses two), or 0 for plain kernel launches with device-side early exit of the rebuild
  * kernels (the baseline launch mode).  MD_EINVAL for a negative value. */

@@ -85,7 +85,6 @@ struct Ctrl {
     int q1, q2;         // replica queue cursors of the replica-resident kernel
     int rep_overflow;   // a replica-resident build overflowed (results stay exact; grow n_max)
     int pad;
-    unsigned long long last_pass_step;   // fused rebuild: last step (+1) whose pass was counted
 };
 
 template <typename R> struct StepArgs {
@@ -171,8 +170,6 @@ template <typename R> struct RebuildArgs {
     int sort_nmax, sort_cmax;
     size_t sort_smem;
     int launch_prio;         // host side: CUDA launch priority of these launches (0 = default)
-    int fused;               // 1: one CTA per replica sorts and builds in shared memory
-    size_t fused_smem;       // its dynamic shared memory
     int list_method;         // 0 sorted cells (Sec. 7), 1 O(N^2) scan (Sec. 6)
     int resort;              // O(N^2) method: every resort-th pass sorts by cell (0 never)
     const SysDesc *sys;
@@ -194,12 +191,7 @@ template <typename R> cudaError_t launch_rebuild_timed(const RebuildArgs<R> &a, 
                                                        cudaEvent_t e0, cudaEvent_t e1);
 cudaError_t launch_arm(const Ctrl *ctrl, cudaGraphConditionalHandle h, cudaStream_t s);
 template <typename R> cudaError_t prepare_sort_small(size_t smem);
-template <typename R> cudaError_t prepare_rebuild_fused(size_t smem);
-// Dynamic shared memory of the fused rebuild (k_rebuild_rep) for replicas of up to nmax particles
-// and cmax cells: positions, cell starts and counters, per-particle cell and permutation.
-inline size_t rebuild_fused_smem_bytes(int nmax, int cmax, size_t r4) {
-    return (size_t)nmax * r4 + (size_t)(2 * cmax + 1) * 4 + (size_t)2 * nmax * 4;
-}
+
 inline size_t sort_small_smem_bytes(int nmax, int cmax) {
     return (size_t)(2 * cmax + 1 + 3 * nmax) * 4;
 }

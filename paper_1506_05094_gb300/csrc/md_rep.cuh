@@ -93,16 +93,15 @@ __device__ __forceinline__ void block_scan_cells(const int *cnt, int *start, int
 // counts (cellStart), scatter, in-cell order by user id, permutation of all particle data, and the
 // list build of Fig. 4 from the shared-memory positions and cell starts (TPB lanes per particle).
 // On entry s_pos holds the replica's positions in its current slot order; on exit the sorted
-// ones, s_cs the cell starts (local slots).  write_pos: also store the sorted positions in the
-// global mirror b.pos (a later kernel reads them there).  An overfull list stores n_max entries,
-// raises *ovf_flag and the largest count, and the call returns 1 (block-uniform); else 0.
+// ones, s_cs the cell starts (local slots).  An overfull list stores n_max entries, raises
+// *ovf_flag and the largest count, and the call returns 1 (block-uniform); else 0.
 // The slot order, list order and list contents are those of the grid path's sort and build.
 // Call with the whole block; uses s_cnt (cmax), s_cell and s_perm (n entries each), s_warp (32).
 template <typename R, int TPB>
 __device__ __forceinline__ int cta_rebuild(const RebuildArgs<R> &b, const SysDesc &S, int r,
                                            typename V4T<R>::t *s_pos, int *s_cs, int *s_cnt,
                                            int *s_cell, int *s_perm, int *s_warp, const R *s_thr,
-                                           bool write_pos, int *ovf_flag) {
+                                           int *ovf_flag) {
     const int n = S.n, off = S.off;
     const int C = S.nc * S.nc * S.nc;
     for (int c = threadIdx.x; c < C; c += blockDim.x) s_cnt[c] = 0;
@@ -142,7 +141,6 @@ __device__ __forceinline__ int cta_rebuild(const RebuildArgs<R> &b, const SysDes
     for (int q = threadIdx.x; q < n; q += blockDim.x) {
         const int d = off + q;
         s_pos[q] = b.tpos[d];
-        if (write_pos) b.pos[d] = s_pos[q];
         b.xd[d] = b.txd[d]; b.yd[d] = b.tyd[d]; b.zd[d] = b.tzd[d];
         b.vel[d] = b.tvel[d];
         b.img[d] = b.timg[d];
@@ -253,7 +251,7 @@ __global__ void __launch_bounds__(1024) k_rep(const StepArgs<R> a, const Rebuild
         if (rebuild) {
             // ---- Sec. 7 rebuild inside the CTA: bin, scan, scatter, order by id, permute, build
             if (cta_rebuild<R, TPB>(b, S, r, s_pos, s_cs, s_cnt, s_cell, s_perm, s_warp, s_thr,
-                                    false, &a.ctrl->rep_overflow) &&
+                                    &a.ctrl->rep_overflow) &&
                 threadIdx.x == 0)
                 s_ovf = 1;
             __syncthreads();
@@ -279,7 +277,7 @@ __global__ void __launch_bounds__(1024) k_rep(const StepArgs<R> a, const Rebuild
                 if (!direct) {
                     SharedPos<R> src{s_pos, off};
                     force_sum<R, TP, SINGLE, SharedPos<R>, false>(a, src, i, ri, ti, F, lt, s_c0,
-                                                                 s_c1, fx, fy, fz, u, w);
+                                                                 s_c1, fx, fy, fz, u, w, nullptr, &S);
                 } else {
                     force_direct<R, TP, SINGLE>(a, S, s_pos, s_cs, li, ri, ti, F, lt, s_c0, s_c1,
                                                 fx, fy, fz, u, w);
@@ -382,44 +380,5 @@ template <typename R> __global__ void __launch_bounds__(1024) k_sort_small(const
     }
 }
 
-
-// ------------------------------------------------------------------------------------------------
-// Fused rebuild of the grid path for batches of replicas: one CTA per replica (grid = replicas);
-// a CTA whose replica keeps its list exits at once, the others run the whole Sec. 7 rebuild of
-// their replica in shared memory (cta_rebuild: sort, permutation, list build) and write the sorted
-// positions back to the mirror for the step kernel that follows.  This replaces the plan / sort /
-// build chain of grid-wide kernels with one launch whose flagged CTAs each stay on one SM, so the
-// step of the replicas that keep their list keeps the rest of the GPU.  The lists are the grid
-// chain's, bit for bit.  The first flagged CTA of a step counts the rebuild pass.
-// ------------------------------------------------------------------------------------------------
-template <typename R, int TPB>
-__global__ void __launch_bounds__(512) k_rebuild_rep(const RebuildArgs<R> b) {
-    typedef typename V4T<R>::t V4;
-    extern __shared__ __align__(16) unsigned char smem_fr[];
-    __shared__ R s_thr[MD_MAX_PAIRS];
-    __shared__ int s_warp[32];
-    __shared__ SysDesc S;
-    const int r = blockIdx.x;
-    if (rebuild_off(b.ctrl) || !b.need_in[r]) return;   // block-uniform
-    V4 *s_pos = reinterpret_cast<V4 *>(smem_fr);
-    int *s_cs = reinterpret_cast<int *>(s_pos + b.sort_nmax);   // cmax + 1
-    int *s_cnt = s_cs + b.sort_cmax + 1;                         // cmax
-    int *s_cell = s_cnt + b.sort_cmax;                           // nmax
-    int *s_perm = s_cell + b.sort_nmax;                          // nmax
-    const int npair = b.ntypes * b.ntypes;
-    for (int p = threadIdx.x; p < npair; p += blockDim.x)
-        s_thr[p] = sizeof(R) == 4 ? (R)b.tab[p].thr2 : (R)b.tab[p].thr2d;
-    if (threadIdx.x == 0) {
-        S = b.sys[r];
-        // one rebuild pass per step: the first flagged CTA of this step counts it
-        const unsigned long long next = (unsigned long long)b.ctrl->step + 1ull;
-        if (atomicMax(&b.ctrl->last_pass_step, next) < next) b.ctrl->rebuild_passes += 1;
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < S.n; k += blockDim.x) s_pos[k] = b.pos[S.off + k];
-    __syncthreads();
-    cta_rebuild<R, TPB>(b, S, r, s_pos, s_cs, s_cnt, s_cell, s_perm, s_warp, s_thr, true,
-                        &b.ctrl->overflow);
-}
 
 }  // namespace md

@@ -74,9 +74,6 @@ struct md_sim {
     int rep_threads = 512, rep_ctas = 1;
     bool sort_small = false;
     size_t sort_smem = 0;
-    bool fused_ok = false;    // the fused per-replica rebuild fits the largest replica
-    size_t fused_smem = 0;
-    int rebuild_kind = 0;     // 0 auto, 1 kernel chain, 2 fused per-replica rebuild
     bool staged_ok = false;   // path 3: grid step kernel with replica positions in shared memory
     size_t staged_smem = 0;
     int rep_nmax = 0, rep_cmax = 0;
@@ -241,18 +238,6 @@ int configure_layout(md_sim *s, bool realloc_cells) {
         cudaGetLastError();
     }
     {
-        // fused per-replica rebuild: the largest replica's sort and build in one CTA's shared
-        // memory (512 threads, up to 16384 particles)
-        int optin4 = 0;
-        cudaDeviceGetAttribute(&optin4, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
-        s->fused_smem = rebuild_fused_smem_bytes(s->rep_nmax, s->rep_cmax, s->r4);
-        s->fused_ok = s->rep_nmax <= 16384 && s->fused_smem + 2048 <= (size_t)optin4 &&
-                      (s->precision == MD_FP64 ? prepare_rebuild_fused<double>(s->fused_smem)
-                                               : prepare_rebuild_fused<float>(s->fused_smem)) ==
-                          cudaSuccess;
-        cudaGetLastError();
-    }
-    {
         int optin3 = 0;
         cudaDeviceGetAttribute(&optin3, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
         s->staged_smem = (size_t)s->rep_nmax * 16;
@@ -379,13 +364,6 @@ template <typename R> StepArgs<R> step_args(md_sim *s, int parity, int force_onl
     return a;
 }
 
-// The fused per-replica rebuild (k_rebuild_rep) replaces the grid chain of the cell method when
-// asked for, or automatically for batches of 8 or more replicas that fit in shared memory.
-bool use_fused(const md_sim *s) {
-    if (s->list_method != 0 || !s->fused_ok) return false;
-    return s->rebuild_kind == 2 || (s->rebuild_kind == 0 && s->R >= 8);
-}
-
 template <typename R> RebuildArgs<R> rebuild_args(md_sim *s, int parity, const void *key) {
     typedef typename V4T<R>::t V4;
     RebuildArgs<R> a;
@@ -421,8 +399,6 @@ template <typename R> RebuildArgs<R> rebuild_args(md_sim *s, int parity, const v
     a.nsm = s->nsm;
     a.tpb = s->tpb;
     a.sort_small = s->sort_small ? 1 : 0;
-    a.fused = (use_fused(s) && key == nullptr) ? 1 : 0;   // a restore keys on other positions
-    a.fused_smem = s->fused_smem;
     a.list_method = s->list_method == 1 ? 1 : 0;
     a.resort = s->list_method == 1 ? s->resort : 0;
     a.sort_nmax = s->rep_nmax;
@@ -1404,16 +1380,6 @@ int md_set_path(md_sim *s, int path) {
     return MD_OK;
 }
 
-int md_set_rebuild_kernel(md_sim *s, int kind) {
-    if (!s || kind < 0 || kind > 2) return MD_EINVAL;
-    if (s->sticky) return s->sticky;
-    if (kind == 2 && !s->fused_ok) return MD_EINVAL;
-    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(s, MD_ECUDA);
-    destroy_graphs(s);
-    s->rebuild_kind = kind;
-    return MD_OK;
-}
-
 int md_set_graph_block(md_sim *s, int steps) {
     if (!s) return MD_EINVAL;
     if (steps < 0) return MD_EINVAL;
@@ -1450,7 +1416,7 @@ int md_get_stats(md_sim *s, md_stats *out) {
     out->reach = s->reach;
     out->build_lanes = s->tpb;
     out->path = use_rep(s) ? 2 : ((s->path == 3 && s->staged_ok) ? 3 : 1);
-    const int cell_kernels = use_fused(s) ? 1 : (s->sort_small ? 3 : 7);   // plan, sort, build
+    const int cell_kernels = s->sort_small ? 3 : 7;   // plan, sort (1 or 5 kernels), build
     out->rebuild_kernels = s->list_method == 2   ? 0
                            : s->list_method == 0 ? cell_kernels
                            : s->resort > 0       ? cell_kernels + 1

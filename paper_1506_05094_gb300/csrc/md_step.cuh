@@ -31,41 +31,49 @@ template <bool NC> __device__ __forceinline__ int ld_idx(const int *p) {
 
 // NC: the list may be read through the non-coherent read-only path (it was written by an
 // earlier kernel); false when the same kernel has just built it.
+// A position half a box away from ri along x: outside every cutoff (L > 2 (range + s)), of the
+// same type, so a masked entry of the force loop contributes exact zeros.
+template <typename V4> __device__ __forceinline__ V4 far_from(const V4 &ri, const SysDesc &S);
+template <> __device__ __forceinline__ float4 far_from<float4>(const float4 &ri, const SysDesc &S) {
+    return make_float4(ri.x + S.halfLf, ri.y, ri.z, ri.w);
+}
+template <> __device__ __forceinline__ double4_32a far_from<double4_32a>(const double4_32a &ri,
+                                                                         const SysDesc &S) {
+    return make_double4_32a(ri.x + 0.5 * S.L, ri.y, ri.z, ri.w);
+}
 template <typename R, int TP, bool SINGLE, typename Src, bool NC = true, int SF = 0>
 __device__ __forceinline__ void force_sum(const StepArgs<R> &a, const Src &P4, int i,
                                           const typename V4T<R>::t &ri, int ti, const Frame<R> &F,
                                           int lt, const typename Coef4<R>::t *s_c0,
                                           const typename Coef4<R>::t *s_c1, R &fx, R &fy, R &fz,
                                           R &u, R &w,
-                                          const typename Coef4<R>::t *s_cq = nullptr) {
+                                          const typename Coef4<R>::t *s_cq = nullptr,
+                                          const SysDesc *Sp = nullptr) {
     typedef typename V4T<R>::t V4;
     const typename Coef4<R>::t c1 = s_c0[0];
     const typename Coef4<R>::t c1b = s_c1[0];
     const int nn = a.nnb[i];
-    // sliced column-major list: neighbour k of slot i at ((i/32)*nmax + k)*32 + i%32
+    const int m = nn > lt ? (nn - lt + TP - 1) / TP : 0;   // entries of this lane
     const int stride = TP * 32;
     const int *q = a.nbl + nbl_offset(i, lt, a.nmax);
-    int k = lt;
-    int j0 = 0, j1 = 0, j2 = 0, j3 = 0;
-    if (k + 3 * TP < nn) {
-        j0 = ld_idx<NC>(q); j1 = ld_idx<NC>(q + stride); j2 = ld_idx<NC>(q + 2 * stride); j3 = ld_idx<NC>(q + 3 * stride);
-    }
-    for (; k + 3 * TP < nn; k += 4 * TP) {
-        const V4 r0 = P4(j0), r1 = P4(j1), r2 = P4(j2), r3 = P4(j3);
+    const V4 far = far_from(ri, *Sp);
+    // groups of four entries, the indices of the next group loaded while this one is evaluated;
+    // entries past the end of the lane's list read the far position instead (no remainder loop:
+    // a lane's last, partial group costs one pass of the loop, not up to three dependent ones)
+    int j0 = 0 < m ? ld_idx<NC>(q) : -1, j1 = 1 < m ? ld_idx<NC>(q + stride) : -1;
+    int j2 = 2 < m ? ld_idx<NC>(q + 2 * stride) : -1, j3 = 3 < m ? ld_idx<NC>(q + 3 * stride) : -1;
+    for (int e = 0; e < m; e += 4) {
+        const V4 r0 = j0 >= 0 ? P4(j0) : far, r1 = j1 >= 0 ? P4(j1) : far;
+        const V4 r2 = j2 >= 0 ? P4(j2) : far, r3 = j3 >= 0 ? P4(j3) : far;
         q += 4 * stride;
-        if (k + 7 * TP < nn) {   // prefetch the next four indices (Sec. 5 prefetching)
-            j0 = ld_idx<NC>(q); j1 = ld_idx<NC>(q + stride); j2 = ld_idx<NC>(q + 2 * stride);
-            j3 = ld_idx<NC>(q + 3 * stride);
-        }
+        j0 = e + 4 < m ? ld_idx<NC>(q) : -1;
+        j1 = e + 5 < m ? ld_idx<NC>(q + stride) : -1;
+        j2 = e + 6 < m ? ld_idx<NC>(q + 2 * stride) : -1;
+        j3 = e + 7 < m ? ld_idx<NC>(q + 3 * stride) : -1;
         interact<R, SINGLE, SF>(ri, ti, r0, F, a.ntypes, s_c0, s_c1, c1, c1b, fx, fy, fz, u, w, s_cq);
         interact<R, SINGLE, SF>(ri, ti, r1, F, a.ntypes, s_c0, s_c1, c1, c1b, fx, fy, fz, u, w, s_cq);
         interact<R, SINGLE, SF>(ri, ti, r2, F, a.ntypes, s_c0, s_c1, c1, c1b, fx, fy, fz, u, w, s_cq);
         interact<R, SINGLE, SF>(ri, ti, r3, F, a.ntypes, s_c0, s_c1, c1, c1b, fx, fy, fz, u, w, s_cq);
-    }
-    for (; k < nn; k += TP) {
-        const int j = ld_idx<NC>(q);
-        q += stride;
-        interact<R, SINGLE, SF>(ri, ti, P4(j), F, a.ntypes, s_c0, s_c1, c1, c1b, fx, fy, fz, u, w, s_cq);
     }
 }
 
@@ -211,8 +219,8 @@ __device__ __forceinline__ void pair_add(float &h, float &l, float rh, float rl)
     l = __fadd_rn(__fadd_rn(l, rl), e);
 }
 
-// Warp sums of the MD_NRED per-particle quantities, each accurate to FP64 precision, in lane 0's
-// out[q] (the other lanes' out[] is unspecified).  Mixed precision: the FP32 values are summed as exact float pairs (hi + lo) in a
+// Warp sums of the MD_NRED per-particle quantities, each accurate to FP64 precision, written to
+// out[q] (shared memory, the warp's row) by one lane each.  Mixed precision: the FP32 values are summed as exact float pairs (hi + lo) in a
 // transposed tree -- at distance 16 each half of the warp keeps half of 8 slots (6 quantities, 2
 // zeros), at 8 a quarter, at 4 an eighth, then every lane adds one slot -- so each lane does 9
 // exact pair additions instead of 30 plain ones, and no FP64 instruction runs in the tree (the
@@ -248,15 +256,9 @@ __device__ __forceinline__ void warp_sums(const float v[MD_NRED], double out[MD_
         const float rl = __shfl_xor_sync(FULL_MASK, l[0], off);
         pair_add(h[0], l[0], rh, rl);
     }
-    // slot 0 of lane 4 q (lane bits 4, 3, 2 = the bits of q) holds quantity q; lane 0 collects
-    // the pairs and forms hi + lo in FP64 (only lane 0's out[] is meaningful)
-#pragma unroll
-    for (int q = 0; q < MD_NRED; ++q) {
-        const float qh = __shfl_sync(FULL_MASK, h[0], 4 * q);
-        const float ql = __shfl_sync(FULL_MASK, l[0], 4 * q);
-        out[q] = 0.0;
-        if (lane == 0) out[q] = (double)qh + (double)ql;
-    }
+    // slot 0 of lane 4 q (lane bits 4, 3, 2 = the bits of q) holds quantity q: those lanes form
+    // hi + lo in FP64 side by side and store it
+    if ((lane & 3) == 0 && (lane >> 2) < MD_NRED) out[lane >> 2] = (double)h[0] + (double)l[0];
 }
 __device__ __forceinline__ void warp_sums(const double v[MD_NRED], double out[MD_NRED]) {
 #pragma unroll
@@ -264,7 +266,7 @@ __device__ __forceinline__ void warp_sums(const double v[MD_NRED], double out[MD
         double x = v[q];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(FULL_MASK, x, o);
-        out[q] = x;
+        if ((threadIdx.x & 31) == 0) out[q] = x;
     }
 }
 
@@ -275,12 +277,8 @@ __device__ __forceinline__ void warp_sums(const double v[MD_NRED], double out[MD
 template <typename R>
 __device__ __forceinline__ void tile_partial(const R vals[MD_NRED], double (*s_tmp)[MD_NRED],
                                              double *out, int tw) {
-    double ws[MD_NRED];
-    warp_sums(vals, ws);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (lane == 0)
-#pragma unroll
-        for (int q2 = 0; q2 < MD_NRED; ++q2) s_tmp[warp][q2] = ws[q2];
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    warp_sums(vals, s_tmp[warp]);
     __syncthreads();
     const int ntile = nw / tw;
     if (threadIdx.x < ntile * MD_NRED) {
@@ -448,7 +446,7 @@ __global__ void __launch_bounds__(1024) k_step(const StepArgs<R> a) {
         if (STAGE) {
             SharedPos<R> src{s_pos, S.off};
             force_sum<R, TP, SINGLE, SharedPos<R>, true, SF>(a, src, i, ri, ti, F, lt, s_c0, s_c1,
-                                                             fx, fy, fz, u, w, s_cq);
+                                                             fx, fy, fz, u, w, s_cq, &S);
         } else if (a.nolist) {
             GlobalPos<R> src{a.pos_in};
             force_all<R, TP, SINGLE, SF>(a, src, S, i, ri, ti, F, lt, s_c0, s_c1, fx, fy, fz, u, w,
@@ -456,7 +454,7 @@ __global__ void __launch_bounds__(1024) k_step(const StepArgs<R> a) {
         } else {
             GlobalPos<R> src{a.pos_in};
             force_sum<R, TP, SINGLE, GlobalPos<R>, true, SF>(a, src, i, ri, ti, F, lt, s_c0, s_c1,
-                                                             fx, fy, fz, u, w, s_cq);
+                                                             fx, fy, fz, u, w, s_cq, &S);
         }
     }
     merge_lanes<R, TP>(fx, fy, fz, u, w);

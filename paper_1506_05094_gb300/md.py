@@ -28,7 +28,7 @@ SYMBOLS = ("md_create", "md_set_integrator", "md_set_state", "md_set_stream", "m
            "md_set_tuning", "md_get_tuning", "md_set_skin", "md_get_skin", "md_set_list_capacity",
            "md_set_path", "md_set_list_method", "md_set_coulomb", "md_set_rebuild_batch",
            "md_set_resort_interval",
-           "md_set_graph_block", "md_set_rebuild_kernel", "md_autotune",
+           "md_set_graph_block", "md_autotune",
            "md_get_stats", "md_profile", "md_set_log", "md_get_log", "md_checkpoint_size",
            "md_save_checkpoint", "md_load_checkpoint", "md_destroy", "md_strerror",
            "md_forces_static", "md_measure_fp32_peak")
@@ -106,7 +106,6 @@ def lib():
         "md_set_rebuild_batch": [p, i],
         "md_set_resort_interval": [p, i],
         "md_set_graph_block": [p, i],
-        "md_set_rebuild_kernel": [p, i],
         "md_autotune": [p, C.c_char_p, i, i],
         "md_set_skin": [p, d],
         "md_get_skin": [p, pd],
@@ -264,11 +263,6 @@ class Sim:
         """'auto' / 'grid' / 'replica' / 'staged' (or 0 / 1 / 2 / 3)."""
         code = {"auto": 0, "grid": 1, "replica": 2, "staged": 3}.get(path, path)
         _ck(lib().md_set_path(self._h, int(code)), "md_set_path")
-
-    def set_rebuild_kernel(self, kind):
-        """"auto", "chain" (grid-wide kernels) or "fused" (one CTA per replica)."""
-        k = {"auto": 0, "chain": 1, "fused": 2}[kind] if isinstance(kind, str) else int(kind)
-        _ck(lib().md_set_rebuild_kernel(self._h, k), "md_set_rebuild_kernel")
 
     def set_graph_block(self, steps: int):
         _ck(lib().md_set_graph_block(self._h, int(steps)), "md_set_graph_block")

@@ -295,52 +295,6 @@ def test_split_graph_steps_bit_identical_to_plain_launches():
     assert outs[0][1] == outs[1][1]
 
 
-@pytest.mark.parametrize("gb", [20, 0])
-def test_fused_rebuild_bit_identical_to_kernel_chain(gb):
-    """The fused per-replica rebuild (one CTA per flagged replica sorts and builds in shared
-    memory) gives the kernel chain's lists, hence its trajectory, bit for bit: 12 replicas of
-    uneven size, NVT, 300 steps with many rebuilds, in split graph steps and in plain launches."""
-    sts = [ka(n, seed=800 + k) for k, n in enumerate([512, 3000, 600, 900, 4096, 650, 1000, 550,
-                                                      750, 2048, 777, 1500])]
-    outs = []
-    for kind in ("fused", "chain"):
-        with make_sim(KA, sts, integrator="nvt", dt=0.0025, T=0.8, graph_block=gb) as sim:
-            sim.set_path("grid")
-            sim.set_rebuild_kernel(kind)
-            sim.step(300)
-            st = sim.stats()
-            assert st["rebuild_kernels"] == (1 if kind == "fused" else 3)
-            assert st["replica_rebuilds"] > 3 * len(sts)
-            outs.append(([sim.get_state(r) for r in range(len(sts))],
-                         [sim.energies(r) for r in range(len(sts))], st))
-    for x, y in zip(outs[0][0], outs[1][0]):
-        for u, v in zip(x, y):
-            np.testing.assert_array_equal(u, v)
-    for x, y in zip(outs[0][1], outs[1][1]):
-        assert x["U"] == y["U"] and x["xi"] == y["xi"] and x["W"] == y["W"]
-    assert outs[0][2]["replica_rebuilds"] == outs[1][2]["replica_rebuilds"]
-    assert outs[0][2]["rebuild_passes"] == outs[1][2]["rebuild_passes"]
-
-
-def test_fused_rebuild_matches_oracle():
-    """Fused rebuild: pair sets equal the oracle's FP32 brute force bit for bit at the start (the
-    first build), and forces match the oracle after 60 NVT steps with rebuilds."""
-    sts = [ka(n, seed=900 + k) for k, n in enumerate([700, 1300, 520, 2600, 900, 1111, 640, 800])]
-    with make_sim(KA, sts, integrator="nvt", dt=0.0025, T=0.8, graph_block=10) as sim:
-        sim.set_rebuild_kernel("fused")
-        for r, st in enumerate(sts):
-            sim.forces(r)                      # the first build, from the loaded positions
-            counts, nb = sim.neighbors(r)
-            ref, rc = oracle.neighbors_fp32(f32(st.pos), st.types, st.L, KA, 0.3)
-            np.testing.assert_array_equal(counts, rc)
-            for i in range(st.n):
-                np.testing.assert_array_equal(np.sort(nb[i, :counts[i]]), ref[i])
-        sim.step(60)
-        assert sim.stats()["replica_rebuilds"] > 2 * len(sts)
-        for r, st in enumerate(sts):
-            _check_forces(sim, st, KA, r=r, pos_dev=f32(sim.get_state(r)[0]))
-
-
 def test_batched_replicas_equal_single_runs():
     """Replicas inside a batch follow exactly (bitwise) the trajectory they follow alone."""
     sts = [ka(n, seed=30 + k) for k, n in enumerate([512, 700, 1024, 900])]

@@ -73,13 +73,16 @@ def _boundary_state(st, rng):
     whole periods added or removed; returns the input and the same positions folded into [0, L)
     the way the library folds them (L itself maps to 0)."""
     L = st.L
-    pos = st.pos.copy()
-    n = len(pos)
+    n = len(st.pos)
+    # the random start is a jittered cubic lattice with planes at (i + 1/2) a: shifting every
+    # coordinate by a/2 puts a plane of particles on each face (a valid periodic configuration)
+    a = L / int(np.ceil(n ** (1.0 / 3.0) - 1e-12))
+    pos = np.mod(st.pos - 0.5 * a, L)
     specials = [L, -1e-17, L - 1e-15, 0.0, -0.0, np.nextafter(L, 0.0), 1e-300]
     k = 0
     for d in range(3):
-        # particles already within 0.3 of a face move onto it (no new close contacts)
-        near = np.flatnonzero(np.minimum(pos[:, d], L - pos[:, d]) < 0.3)
+        # particles within 0.1 of a face move onto it (no new close contacts)
+        near = np.flatnonzero(np.minimum(pos[:, d], L - pos[:, d]) < 0.1)
         for i in rng.permutation(near)[:15]:
             pos[i, d] = specials[k % len(specials)]
             k += 1
