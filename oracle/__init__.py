@@ -10,6 +10,7 @@ Every function takes numpy arrays and returns numpy arrays; nothing here touches
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 import sys
@@ -62,12 +63,12 @@ def lib():
         L.or_run.argtypes = [C.c_int, d, d, i, C.c_double, C.c_int, d, d, d, d, C.c_int,
                              C.c_double, C.c_double, C.c_double, d, C.c_int, d, C.c_int]
         L.or_neighbors_fp64.argtypes = [C.c_int, d, i, C.c_double, C.c_int, d, C.c_int, i, i]
-        L.or_neighbors_fp32.argtypes = [C.c_int, f, i, C.c_float, C.c_float, C.c_int, f, C.c_int,
-                                        i, i]
+        u32 = C.POINTER(C.c_uint32)
+        L.or_neighbors_fixed.argtypes = [C.c_int, u32, i, C.c_float, C.c_int, f, C.c_int, i, i]
         for name in ("or_pair", "or_set_threads"):
             getattr(L, name).restype = None
         for name in ("or_forces", "or_forces_cells", "or_forces_subset", "or_run",
-                     "or_neighbors_fp64", "or_neighbors_fp32"):
+                     "or_neighbors_fp64", "or_neighbors_fixed"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -228,23 +229,52 @@ def fp32_threshold(model, skin):
     return ((_list_rc(model) + skin) ** 2).astype(np.float32).ravel()
 
 
-def neighbors_fp32(posf, types, L, model, skin, maxn=None):
-    """Brute-force neighbour sets in the bit-defined FP32 arithmetic (see md_oracle.c)."""
-    posf = np.ascontiguousarray(posf, dtype=np.float32)
+def device_grid(pos, L):
+    """The mixed-precision device's fixed-point image of positions -- the representation the list
+    rule and the pair arithmetic start from, restated here from its definition:
+      1. fold each coordinate into [0, L): v = x - floor(x / L) L, then fold a result at or above
+         L (subtract L) or below 0 (add L), and map a value still equal to L to 0;
+      2. master = round-half-even(v / L 2^64) as an unsigned 64-bit integer, 2^64 itself -> 0;
+      3. mirror q = (master + 2^31) / 2^32 rounded down, modulo 2^32 (the master rounded to the
+         nearest 32-bit grid point).
+    Returns q (n,3) uint32 and the mirror positions q L / 2^32 in FP64."""
+    x = np.array(pos, dtype=np.float64, copy=True)
+    L = float(L)
+    v = x - np.floor(x / L) * L
+    v = np.where(v >= L, v - L, v)
+    v = np.where(v < 0.0, v + L, v)
+    v = np.where(v >= L, 0.0, v)
+    m = np.rint(np.ldexp(v / L, 64))
+    m = np.where(m >= 2.0 ** 64, 0.0, np.maximum(m, 0.0))
+    master = m.astype(np.uint64)
+    with np.errstate(over="ignore"):
+        q = ((master + np.uint64(2 ** 31)) >> np.uint64(32)) & np.uint64(0xFFFFFFFF)
+    q = q.astype(np.uint32)
+    return q, q.astype(np.float64) * math.ldexp(L, -32)
+
+
+def mirror_ps2(L):
+    """(float)((L / 2^32)^2), the squared mirror unit of the fixed-point list rule."""
+    u = math.ldexp(float(L), -32)
+    return np.float32(u * u)
+
+
+def neighbors_fixed(q, types, L, model, skin, maxn=None):
+    """Brute-force neighbour sets in the bit-defined fixed-point arithmetic (see md_oracle.c) of
+    the mirror q (n,3) uint32 (device_grid)."""
+    q = np.ascontiguousarray(q, dtype=np.uint32)
     types = np.ascontiguousarray(types, dtype=np.int32)
-    n = posf.shape[0]
+    n = q.shape[0]
     nt = int(model.n_types)
     thr2 = np.ascontiguousarray(fp32_threshold(model, skin))
     maxn = n if maxn is None else maxn
     counts = np.zeros(n, dtype=np.int32)
     lst = np.zeros((n, max(maxn, 1)), dtype=np.int32)
-    Lf = np.float32(L)
-    invLf = np.float32(1.0 / float(L))
-    r = lib().or_neighbors_fp32(n, _p(posf, C.c_float), _p(types, C.c_int), C.c_float(Lf),
-                                C.c_float(invLf), nt, _p(thr2, C.c_float), maxn,
-                                _p(counts, C.c_int), _p(lst, C.c_int))
+    r = lib().or_neighbors_fixed(n, q.ctypes.data_as(C.POINTER(C.c_uint32)), _p(types, C.c_int),
+                                 C.c_float(mirror_ps2(L)), nt, _p(thr2, C.c_float), maxn,
+                                 _p(counts, C.c_int), _p(lst, C.c_int))
     if r:
-        raise ValueError(f"or_neighbors_fp32 failed ({r})")
+        raise ValueError(f"or_neighbors_fixed failed ({r})")
     return [lst[i, :min(counts[i], maxn)].copy() for i in range(n)], counts
 
 

@@ -16,8 +16,8 @@
  *   - Leapfrog NVE and Nose-Hoover NVT integration (Sec. 2, "Integrators"; the paper names the
  *     integrators but prints no equations: the discretisation used is listed below).
  *   - Brute-force Verlet neighbour sets: j is a neighbour of i iff j != i and the squared
- *     distance is strictly below (rc_ab + s)^2 (Sec. 3 and Figs. 3-4), in FP64 and in a
- *     bit-defined FP32 arithmetic.
+ *     distance is strictly below (rc_ab + s)^2 (Sec. 3 and Figs. 3-4), in FP64 and in the
+ *     bit-defined fixed-point arithmetic of the mixed-precision position mirror.
  *   - Optionally, a Coulomb term between charged particles cut off with the shifted-force method
  *     (Sec. 9 "Electrostatics": the molten-salt benchmark uses Coulomb forces with a large
  *     shifted-force cutoff instead of a mesh/Ewald method).
@@ -42,9 +42,12 @@
  *            v_{n+1/2} = [(1 - xi_n dt/2) v_{n-1/2} + dt F_n / m] / (1 + xi_n dt/2),
  *            r_{n+1} = r_n + dt v_{n+1/2}.
  *            Conserved: H = U + K + g T0 (tau^2 xi^2 / 2 + sum_k xi_k dt).
- *   FP32 neighbour arithmetic: from float positions, d = x_j - x_i; d = d - L*rintf(d*invL)
- *   (each product and difference rounded separately, no fused multiply-add), then
- *   dist2 = (dx*dx + dy*dy) + dz*dz, compared with the FP32 threshold (float)((rc_ab+s)^2).
+ *   Fixed-point neighbour arithmetic (the mixed-precision mirror): each coordinate is a 32-bit
+ *   unsigned integer q with q L / 2^32 the position, so one period is 2^32 units; per axis
+ *   d = (float)(int32)(q_j - q_i) (the 32-bit difference is the nearest periodic image; the
+ *   conversion rounds to nearest), then dist2 = ((dx*dx + dy*dy) + dz*dz) * ps2 in float, each
+ *   product and sum rounded separately (no fused multiply-add), with ps2 = (float)((L / 2^32)^2),
+ *   compared with the FP32 threshold (float)((rc_ab + s)^2).
  *
  * Build: gcc -O2 -fopenmp -ffp-contract=off -fno-fast-math -fPIC -shared (see build.py).
  */
@@ -378,29 +381,29 @@ int or_neighbors_fp64(int n, const double *pos, const int *type, double L, int n
     return 0;
 }
 
-/* FP32 mode: same rule, in the bit-defined FP32 arithmetic stated in the header.  posf is
- * (n,3) float; Lf = (float)L, invLf = (float)(1/L); thr2f[p] = (float)((rc_p + s)^2). */
-static inline float min_image_f(float d, float Lf, float invLf) {
-    float t = d * invLf;
-    t = rintf(t);
-    t = Lf * t;
-    return d - t;
+/* Fixed-point mode: same rule, in the bit-defined arithmetic of the fixed-point mirror stated in
+ * the header.  q is (n,3) uint32; ps2 = (float)((L / 2^32)^2); thr2f[p] = (float)((rc_p + s)^2). */
+static inline float fixed_d(uint32_t a, uint32_t b) {
+    const uint32_t u = a - b;     /* modulo 2^32 */
+    const int32_t d = (int32_t)u; /* two's complement: the nearest image */
+    return (float)d;
 }
 
-int or_neighbors_fp32(int n, const float *posf, const int *type, float Lf, float invLf, int nt,
-                      const float *thr2f, int maxn, int *counts, int *list) {
-    if (n < 0 || nt < 1 || nt > OR_MAX_TYPES || !(Lf > 0) || maxn < 0) return 1;
+int or_neighbors_fixed(int n, const uint32_t *q, const int *type, float ps2, int nt,
+                       const float *thr2f, int maxn, int *counts, int *list) {
+    if (n < 0 || nt < 1 || nt > OR_MAX_TYPES || !(ps2 > 0) || maxn < 0) return 1;
 #pragma omp parallel for schedule(dynamic, 16)
     for (int i = 0; i < n; ++i) {
         int c = 0;
         for (int j = 0; j < n; ++j) {
             if (j == i) continue;
-            float dx = min_image_f(posf[3 * j] - posf[3 * i], Lf, invLf);
-            float dy = min_image_f(posf[3 * j + 1] - posf[3 * i + 1], Lf, invLf);
-            float dz = min_image_f(posf[3 * j + 2] - posf[3 * i + 2], Lf, invLf);
+            const float dx = fixed_d(q[3 * j], q[3 * i]);
+            const float dy = fixed_d(q[3 * j + 1], q[3 * i + 1]);
+            const float dz = fixed_d(q[3 * j + 2], q[3 * i + 2]);
             float d2 = dx * dx;
             d2 = d2 + dy * dy;
             d2 = d2 + dz * dz;
+            d2 = d2 * ps2;
             if (d2 < thr2f[type[i] * nt + type[j]]) {
                 if (c < maxn) list[(long)i * maxn + c] = j;
                 ++c;

@@ -23,7 +23,9 @@ SOURCES = ["md_kernels_f32.cu", "md_kernels_f64.cu", "md_runtime.cu", "md_static
 HEADERS = ["md_internal.cuh", "md_kernels.cuh", "md_common.cuh", "md_step.cuh", "md_rebuild.cuh",
            "md_rep.cuh", "md_launch.inc"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
+# host code: no FMA contraction, so x86 and Arm hosts round every product and sum alike
+CFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+                 "-Xcompiler", "-ffp-contract=off", "-I" + INCLUDE]
 
 
 def nvcc() -> str:

@@ -10,10 +10,10 @@ namespace md {
 
 #define FULL_MASK 0xffffffffu
 
-__device__ __forceinline__ int type_of(float4 p) { return __float_as_int(p.w); }
+__device__ __forceinline__ int type_of(int4 p) { return p.w; }
 __device__ __forceinline__ int type_of(double4_32a p) { return (int)__double_as_longlong(p.w); }
 
-__device__ __forceinline__ float4 ld_nc(const float4 *p) { return __ldg(p); }
+__device__ __forceinline__ int4 ld_nc(const int4 *p) { return __ldg(p); }
 __device__ __forceinline__ double4_32a ld_nc(const double4_32a *p) {
     const double2 *q = reinterpret_cast<const double2 *>(p);
     double2 a = __ldg(q), b = __ldg(q + 1);
@@ -26,8 +26,6 @@ __device__ __forceinline__ float4 make_v4(float x, float y, float z, float w) {
 __device__ __forceinline__ double4_32a make_v4(double x, double y, double z, double w) {
     return make_double4_32a(x, y, z, w);
 }
-__device__ __forceinline__ float type_word(float, int t) { return __int_as_float(t); }
-__device__ __forceinline__ double type_word(double, int t) { return __longlong_as_double((long long)t); }
 
 // Sliced column-major neighbour list (32-particle slices): neighbour k of slot i.  Within a
 // slice the first neighbours of all 32 particles are contiguous, then the second, ... (Sec. 5),
@@ -47,19 +45,31 @@ __device__ __forceinline__ double min_image_fast(double d, double L, double invL
     return __fma_rn(-L, q, d);
 }
 
-// Minimum image of the list build, bit-defined: every product and sum rounded on its own.
-__device__ __forceinline__ float min_image_exact(float d, float L, float invL) {
-    float t = rintf(__fmul_rn(d, invL));
-    return __fsub_rn(d, __fmul_rn(L, t));
+// Difference of two fixed-point mirror coordinates as a float in mirror units: the 32-bit
+// difference wraps to the nearest periodic image by itself (2^32 units are one period), and the
+// int -> float conversion rounds to nearest.
+__device__ __forceinline__ float fixed_diff(int a, int b) {
+    return __int2float_rn((int)((unsigned)a - (unsigned)b));
+}
+
+// Squared distance of the list rule, bit-defined (every product and sum rounded on its own, none
+// contracted).  Mixed precision: d = float(x_j - x_i) per axis in mirror units,
+// dist^2 = ((dx dx + dy dy) + dz dz) ps2.  FP64: d = x_j - x_i; d -= L rint(d / L).
+__device__ __forceinline__ float key_dist2(const int4 &ki, const int4 &kj, const SysDesc &S) {
+    const float dx = fixed_diff(kj.x, ki.x), dy = fixed_diff(kj.y, ki.y),
+                dz = fixed_diff(kj.z, ki.z);
+    return __fmul_rn(__fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz)),
+                     S.ps2);
 }
 __device__ __forceinline__ double min_image_exact(double d, double L, double invL) {
     double t = rint(__dmul_rn(d, invL));
     return __dsub_rn(d, __dmul_rn(L, t));
 }
-__device__ __forceinline__ float dist2_exact(float dx, float dy, float dz) {
-    return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-}
-__device__ __forceinline__ double dist2_exact(double dx, double dy, double dz) {
+__device__ __forceinline__ double key_dist2(const double4_32a &ki, const double4_32a &kj,
+                                            const SysDesc &S) {
+    const double dx = min_image_exact(kj.x - ki.x, S.L, S.invL);
+    const double dy = min_image_exact(kj.y - ki.y, S.L, S.invL);
+    const double dz = min_image_exact(kj.z - ki.z, S.L, S.invL);
     return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
 }
 
@@ -140,36 +150,23 @@ __device__ __forceinline__ void coulomb_pair(R dx, R dy, R dz, R r2, const C4 &q
     w += fs * r2;
 }
 
-// Per-particle minimum-image frame.
+// Per-particle minimum-image frame of the force loop.
 //
-// FP32: the plain d - L*rint(d/L) loses up to ulp(L)/2 on pairs that cross the periodic boundary
-// (the difference of a coordinate near L and one near 0 is rounded before L is removed), and
-// (float)L != L adds a systematic offset.  Instead the coordinate near L is shifted by L first,
-// which is exact (Sterbenz), and L - (float)L is folded into the particle's own shifted
-// coordinate once per particle:
-//   t = x_i - x_j;  if |t| > L/2:  d = xa_i - (x_j - n_i L)   else  d = t
-// with, for x_i >= L/2 (partners can only cross upward): xa_i = x_i - L, n_i = 0, and for
-// x_i < L/2: xa_i = x_i + (L - (float)L), n_i = 1 (the partner near L is shifted instead).
-// Five FP32 instructions per dimension, all on the FMA pipe.
-// FP64: the plain rint form is accurate to the FP64 rounding of the coordinates.
+// Mixed precision: the mirror is 32-bit fixed point with 2^32 units per box edge, so the minimum
+// image of x_i - x_j is the 32-bit difference itself (two's-complement wrap), converted to float:
+// two instructions per axis, exact up to the conversion's rounding (2^-24 relative), and no
+// per-particle state.  The pair loop works with d in mirror units: r^2 = |d|^2 ps2 (real units),
+// the force sum accumulates the scalar force times d, and the particle's force is multiplied by
+// the unit ps once at the end (scale_force, after the lanes are merged).
+// FP64: the plain rint form on the FP64 mirror.
 template <typename R> struct Frame;
-template <> struct Frame<float> { float xa, ya, za, nx, ny, nz, half, L; };
+template <> struct Frame<float> { float ps2, ps2_lo; };
 template <> struct Frame<double> { double L, invL; };
 
-__device__ __forceinline__ Frame<float> make_frame(const float4 &ri, const SysDesc &S) {
-    // x_i - L is exact for x_i >= L/2 (Sterbenz); the L - (float)L remainder (Llo) is then
-    // removed from a small number, and added to x_i < L/2 whose crossing partners sit near L.
+__device__ __forceinline__ Frame<float> make_frame(const int4 &, const SysDesc &S) {
     Frame<float> F;
-    const float L = S.Lf, h = S.halfLf, lo = S.Llo;
-    const bool ux = ri.x >= h, uy = ri.y >= h, uz = ri.z >= h;
-    F.xa = ux ? __fsub_rn(__fsub_rn(ri.x, L), lo) : __fadd_rn(ri.x, lo);
-    F.ya = uy ? __fsub_rn(__fsub_rn(ri.y, L), lo) : __fadd_rn(ri.y, lo);
-    F.za = uz ? __fsub_rn(__fsub_rn(ri.z, L), lo) : __fadd_rn(ri.z, lo);
-    F.nx = ux ? 0.0f : 1.0f;
-    F.ny = uy ? 0.0f : 1.0f;
-    F.nz = uz ? 0.0f : 1.0f;
-    F.half = h;
-    F.L = L;
+    F.ps2 = S.ps2;
+    F.ps2_lo = S.ps2_lo;
     return F;
 }
 __device__ __forceinline__ Frame<double> make_frame(const double4_32a &, const SysDesc &S) {
@@ -179,18 +176,11 @@ __device__ __forceinline__ Frame<double> make_frame(const double4_32a &, const S
     return F;
 }
 
-__device__ __forceinline__ float mi_axis(float xi, float xj, float xa, float n, float half,
-                                         float L) {
-    const float t = __fsub_rn(xi, xj);
-    const float e = __fsub_rn(xa, __fmaf_rn(-n, L, xj));
-    return fabsf(t) > half ? e : t;
-}
-
-__device__ __forceinline__ void pair_delta(const Frame<float> &F, const float4 &ri,
-                                           const float4 &rj, float &dx, float &dy, float &dz) {
-    dx = mi_axis(ri.x, rj.x, F.xa, F.nx, F.half, F.L);
-    dy = mi_axis(ri.y, rj.y, F.ya, F.ny, F.half, F.L);
-    dz = mi_axis(ri.z, rj.z, F.za, F.nz, F.half, F.L);
+__device__ __forceinline__ void pair_delta(const Frame<float> &, const int4 &ri, const int4 &rj,
+                                           float &dx, float &dy, float &dz) {
+    dx = fixed_diff(ri.x, rj.x);
+    dy = fixed_diff(ri.y, rj.y);
+    dz = fixed_diff(ri.z, rj.z);
 }
 __device__ __forceinline__ void pair_delta(const Frame<double> &F, const double4_32a &ri,
                                            const double4_32a &rj, double &dx, double &dy,
@@ -199,6 +189,22 @@ __device__ __forceinline__ void pair_delta(const Frame<double> &F, const double4
     dy = min_image_fast(ri.y - rj.y, F.L, F.invL);
     dz = min_image_fast(ri.z - rj.z, F.L, F.invL);
 }
+// r^2 in real units from the pair_delta components (mixed: |d|^2 (ps2 + ps2_lo), so the rounding
+// of the squared unit adds no common scale error to every distance)
+__device__ __forceinline__ float pair_r2(const Frame<float> &F, float dx, float dy, float dz) {
+    const float d2 = dx * dx + dy * dy + dz * dz;
+    return __fmaf_rn(d2, F.ps2, d2 * F.ps2_lo);
+}
+__device__ __forceinline__ double pair_r2(const Frame<double> &, double dx, double dy, double dz) {
+    return dx * dx + dy * dy + dz * dz;
+}
+// A particle's force sum in real units (mixed: the sum was taken over d in mirror units)
+__device__ __forceinline__ void scale_force(const SysDesc &S, float &fx, float &fy, float &fz) {
+    fx = __fmaf_rn(fx, S.ps, fx * S.ps_lo);
+    fy = __fmaf_rn(fy, S.ps, fy * S.ps_lo);
+    fz = __fmaf_rn(fz, S.ps, fz * S.ps_lo);
+}
+__device__ __forceinline__ void scale_force(const SysDesc &, double &, double &, double &) {}
 
 // Potential kind (template POT, a bit set): bit 0 = LJ with the shifted-force cutoff (else
 // shifted potential), bit 1 = shifted-force Coulomb term (s_cq holds its coefficients; only
@@ -216,7 +222,7 @@ __device__ __forceinline__ void interact(const typename V4T<R>::t &ri, int ti,
     constexpr bool SF = (POT & 1) != 0;
     R dx, dy, dz;
     pair_delta(F, ri, rj, dx, dy, dz);
-    const R r2 = dx * dx + dy * dy + dz * dz;
+    const R r2 = pair_r2(F, dx, dy, dz);
     if (sizeof(R) == 4) {
         // FP32: branch-free.  Nearly every warp has some lane inside rc, so a branch saves no
         // work; without it the compiler interleaves the unrolled candidates' arithmetic.  A pair

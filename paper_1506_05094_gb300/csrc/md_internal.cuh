@@ -3,11 +3,15 @@
 //
 // Layout (all per-particle arrays are indexed by the device's cell-sorted slot; replica r owns
 // slots [off_r, off_r + n_r), and the order inside a replica is (cell, user id)):
-//   pos[2]      : Real4 mirror of the positions, x,y,z plus the type in .w (float bits of the
-//                 int for FP32, the int's bits in the double for FP64); ping-pong by step parity
-//   xd,yd,zd    : FP64 master positions, wrapped into [0, L)
+//   pos[2]      : position mirror, ping-pong by step parity.  Mixed precision: int4 of 32-bit
+//                 fixed-point coordinates (unit L / 2^32, so 2^32 units are one period and the
+//                 minimum image of a difference is its wrap to int32) and the type in .w.
+//                 FP64: double4 with the type's bits in .w
+//   xm,ym,zm    : master positions in [0, L), 8 bytes each.  Mixed precision: 64-bit fixed point
+//                 (unit L / 2^64: the update is an exact integer add and the periodic wrap is the
+//                 add's own wrap-around, no FP64 instruction).  FP64: doubles
 //   img         : int4 periodic image counters (touched only when a particle wraps)
-//   vel         : Real4 velocities v(t - dt/2), .w unused
+//   vel         : Real4 velocities v(t - dt/2), .w unused (float4 / double4)
 //   id          : user index inside the replica
 //   pos_build   : Real4 positions at the last list build (rebuild check, Sec. 6)
 //   nbl         : int32 neighbour slots, column-major within 32-particle slices: neighbour k of
@@ -23,9 +27,16 @@
 #define MD_LOG_COLS 11
 #define MD_NRED 6   // reduced quantities per tile: U, W, K, px, py, pz
 
+// position mirror (V4T), velocities and forces (F4T), master positions (MT) per precision
 template <typename R> struct V4T;
-template <> struct V4T<float> { typedef float4 t; };
+template <> struct V4T<float> { typedef int4 t; };
 template <> struct V4T<double> { typedef double4_32a t; };
+template <typename R> struct F4T;
+template <> struct F4T<float> { typedef float4 t; };
+template <> struct F4T<double> { typedef double4_32a t; };
+template <typename R> struct MT;
+template <> struct MT<float> { typedef unsigned long long t; };
+template <> struct MT<double> { typedef double t; };
 
 // Per replica description (device array, read-only inside a step).
 struct SysDesc {
@@ -35,8 +46,13 @@ struct SysDesc {
     int reach;             // stencil half width in cells
     int span;              // cells visited per dimension (min(2 reach + 1, nc))
     double L, invL;
-    float Lf, invLf, cell_scale, pad;  // cell_scale = nc / L rounded to float
-    float halfLf, Llo;     // (float)(L/2), L - (float)L rounded to float
+    float Lf, invLf, cell_scale;   // cell_scale = nc / L rounded to float (FP64 mode binning)
+    float s64;             // (float)(2^64 / L): master-position units per unit length (mixed)
+    float ps, ps2;         // (float)(L / 2^32) and (float)((L / 2^32)^2): the mirror unit (mixed)
+    float ps_lo, ps2_lo;   // their rounding remainders: ps + ps_lo and ps2 + ps2_lo are exact to
+                           // ~2^-48, so a length scaled from mirror units carries no systematic
+                           // error of the unit's own rounding
+    float pad2[2];
     double K0;             // (3n - 3) T0 / 2
 };
 
@@ -89,10 +105,12 @@ struct Ctrl {
 
 template <typename R> struct StepArgs {
     typedef typename V4T<R>::t V4;
+    typedef typename F4T<R>::t F4;
+    typedef typename MT<R>::t M;
     const V4 *pos_in;
     V4 *pos_out;
-    double *xd, *yd, *zd;
-    V4 *vel;
+    M *xm, *ym, *zm;
+    F4 *vel;
     int4 *img;
     const V4 *pos_build;
     const int *nbl;
@@ -127,7 +145,7 @@ template <typename R> struct StepArgs {
     int rebuild_batch;        // K: rebuild slots every K steps (1: rebuild exactly when needed)
     unsigned *disp;           // per replica: max |r - r_build|^2 and max one-step |dr|^2 (float bits)
     int force_only;           // 1: write f_out / w_out, no integration and no bookkeeping
-    V4 *f_out;                // fx, fy, fz, u_i
+    F4 *f_out;                // fx, fy, fz, u_i
     R *w_out;
     cudaGraphConditionalHandle next_handle;
     int has_next;
@@ -140,18 +158,20 @@ template <typename R> struct StepArgs {
 
 template <typename R> struct RebuildArgs {
     typedef typename V4T<R>::t V4;
+    typedef typename F4T<R>::t F4;
+    typedef typename MT<R>::t M;
     V4 *pos;                 // current mirror (in/out, permuted)
     const V4 *key;           // positions the cells and the list are built from (== pos normally)
     int key_is_pos;
-    double *xd, *yd, *zd;
-    V4 *vel;
+    M *xm, *ym, *zm;
+    F4 *vel;
     int4 *img;
     int *id;
     V4 *pos_build;
     // scratch
     V4 *tpos, *tkey;
-    double *txd, *tyd, *tzd;
-    V4 *tvel;
+    M *txm, *tym, *tzm;
+    F4 *tvel;
     int4 *timg;
     int *tid;
     int *cell_of, *rank, *perm;

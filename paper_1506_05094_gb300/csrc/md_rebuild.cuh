@@ -31,7 +31,16 @@ __device__ __forceinline__ int find_seg(const int *pfx, int n, int t) {
     return lo;
 }
 
-template <typename V4> __device__ __forceinline__ int cell_index(const V4 &p, const SysDesc &S) {
+// Cell of a mirror position (Sec. 7).  Mixed precision: exact integer binning of the fixed-point
+// coordinate, floor(x nc / 2^32), always in [0, nc).  FP64: floor of the FP32 product x nc / L,
+// clamped to [0, nc).
+__device__ __forceinline__ int cell_index(const int4 &p, const SysDesc &S) {
+    const unsigned nc = (unsigned)S.nc;
+    const int cx = (int)__umulhi((unsigned)p.x, nc), cy = (int)__umulhi((unsigned)p.y, nc),
+              cz = (int)__umulhi((unsigned)p.z, nc);
+    return (cz * S.nc + cy) * S.nc + cx;
+}
+__device__ __forceinline__ int cell_index(const double4_32a &p, const SysDesc &S) {
     const float cs = S.cell_scale;
     int cx = __float2int_rd(__fmul_rn((float)p.x, cs));
     int cy = __float2int_rd(__fmul_rn((float)p.y, cs));
@@ -40,6 +49,17 @@ template <typename V4> __device__ __forceinline__ int cell_index(const V4 &p, co
     cy = min(max(cy, 0), S.nc - 1);
     cz = min(max(cz, 0), S.nc - 1);
     return (cz * S.nc + cy) * S.nc + cx;
+}
+// Position of a particle along one axis relative to its cell c, in cell edges (the clipping of
+// the list build's stencil needs only an estimate: it carries a slack far above these roundings).
+// Mixed precision: the exact fraction in [0, 1).  FP64: x nc / L - c (it may reach 1 where the
+// binning clamped a coordinate that rounded up to L).
+__device__ __forceinline__ float cell_frac(int x, int, const SysDesc &S) {
+    const unsigned lo = (unsigned)((unsigned long long)(unsigned)x * (unsigned)S.nc);
+    return (float)lo * 2.3283064365386963e-10f;   // 2^-32
+}
+__device__ __forceinline__ float cell_frac(double x, int c, const SysDesc &S) {
+    return __fmul_rn((float)x, S.cell_scale) - (float)c;
 }
 
 // One CTA: exclusive scans over replicas of (flagged, particles, cells) -> the pass's work list.
@@ -220,9 +240,9 @@ template <typename R> __global__ void k_gather(const RebuildArgs<R> a) {
         const int o = a.perm[s];
         a.tpos[s] = a.pos[o];
         if (!a.key_is_pos) a.tkey[s] = a.key[o];
-        a.txd[s] = a.xd[o];
-        a.tyd[s] = a.yd[o];
-        a.tzd[s] = a.zd[o];
+        a.txm[s] = a.xm[o];
+        a.tym[s] = a.ym[o];
+        a.tzm[s] = a.zm[o];
         a.tvel[s] = a.vel[o];
         a.timg[s] = a.img[o];
         a.tid[s] = a.id[o];
@@ -248,7 +268,6 @@ __device__ __forceinline__ int build_one(const SysDesc &S, const KeySrc &K, cons
     const unsigned below = (1u << lane) - 1u;
     const V4 ki = K(self);
     const int ti = type_of(ki);
-    const R L = box_L<R>(S), invL = box_invL<R>(S);
     const int nc = S.nc, span = S.span, reach = S.reach;
     const int c = cell_index(ki, S);
     const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
@@ -264,9 +283,9 @@ __device__ __forceinline__ int build_one(const SysDesc &S, const KeySrc &K, cons
     float fxc = 0.f, fyc = 0.f, fzc = 0.f, lim2 = 0.f;
     if (!full) {
         const float cs = S.cell_scale;
-        fxc = __fmul_rn((float)ki.x, cs) - (float)cx;
-        fyc = __fmul_rn((float)ki.y, cs) - (float)cy;
-        fzc = __fmul_rn((float)ki.z, cs) - (float)cz;
+        fxc = cell_frac(ki.x, cx, S);
+        fyc = cell_frac(ki.y, cy, S);
+        fzc = cell_frac(ki.z, cz, S);
         float thr = 0.f;
         for (int t = 0; t < ntypes; ++t) thr = fmaxf(thr, (float)s_thr[ti * ntypes + t]);
         lim2 = thr * cs * cs * 1.001f + 1e-3f;
@@ -326,10 +345,7 @@ __device__ __forceinline__ int build_one(const SysDesc &S, const KeySrc &K, cons
                 ok[uu] = false;
                 if (j < rg.y && j != self) {
                     const V4 kj = K(j);
-                    const R dx = min_image_exact(kj.x - ki.x, L, invL);
-                    const R dy = min_image_exact(kj.y - ki.y, L, invL);
-                    const R dz = min_image_exact(kj.z - ki.z, L, invL);
-                    ok[uu] = dist2_exact(dx, dy, dz) < s_thr[ti * ntypes + type_of(kj)];
+                    ok[uu] = key_dist2(ki, kj, S) < s_thr[ti * ntypes + type_of(kj)];
                 }
             }
 #pragma unroll
@@ -390,9 +406,9 @@ template <typename R, int TPB> __global__ void __launch_bounds__(MD_BUILD_BLOCK)
             a.nnb[i] = cnt;
             a.pos[i] = a.tpos[i];
             a.pos_build[i] = Kp[i];
-            a.xd[i] = a.txd[i];
-            a.yd[i] = a.tyd[i];
-            a.zd[i] = a.tzd[i];
+            a.xm[i] = a.txm[i];
+            a.ym[i] = a.tym[i];
+            a.zm[i] = a.tzm[i];
             a.vel[i] = a.tvel[i];
             a.img[i] = a.timg[i];
             a.id[i] = a.tid[i];
@@ -425,17 +441,13 @@ __global__ void __launch_bounds__(MD_BUILD_BLOCK) k_build_n2(const RebuildArgs<R
         const SysDesc &S = a.sys[r];
         const V4 ki = a.key[i];
         const int ti = type_of(ki);
-        const R L = box_L<R>(S), invL = box_invL<R>(S);
         int cnt = 0;
         for (int b0 = S.off; b0 < S.off + S.n; b0 += TPB) {
             const int j = b0 + lt;
             bool ok = false;
             if (j < S.off + S.n && j != i) {
                 const V4 kj = a.key[j];
-                const R dx = min_image_exact(kj.x - ki.x, L, invL);
-                const R dy = min_image_exact(kj.y - ki.y, L, invL);
-                const R dz = min_image_exact(kj.z - ki.z, L, invL);
-                ok = dist2_exact(dx, dy, dz) < s_thr[ti * a.ntypes + type_of(kj)];
+                ok = key_dist2(ki, kj, S) < s_thr[ti * a.ntypes + type_of(kj)];
             }
             const unsigned m = __ballot_sync(gmask, ok);
             if (ok) {

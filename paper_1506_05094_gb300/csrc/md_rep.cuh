@@ -132,7 +132,7 @@ __device__ __forceinline__ int cta_rebuild(const RebuildArgs<R> &b, const SysDes
     for (int q = threadIdx.x; q < n; q += blockDim.x) {
         const int o = off + s_perm[q], d = off + q;
         b.tpos[d] = s_pos[s_perm[q]];
-        b.txd[d] = b.xd[o]; b.tyd[d] = b.yd[o]; b.tzd[d] = b.zd[o];
+        b.txm[d] = b.xm[o]; b.tym[d] = b.ym[o]; b.tzm[d] = b.zm[o];
         b.tvel[d] = b.vel[o];
         b.timg[d] = b.img[o];
         b.tid[d] = b.id[o];
@@ -141,7 +141,7 @@ __device__ __forceinline__ int cta_rebuild(const RebuildArgs<R> &b, const SysDes
     for (int q = threadIdx.x; q < n; q += blockDim.x) {
         const int d = off + q;
         s_pos[q] = b.tpos[d];
-        b.xd[d] = b.txd[d]; b.yd[d] = b.tyd[d]; b.zd[d] = b.tzd[d];
+        b.xm[d] = b.txm[d]; b.ym[d] = b.tym[d]; b.zm[d] = b.tzm[d];
         b.vel[d] = b.tvel[d];
         b.img[d] = b.timg[d];
         b.id[d] = b.tid[d];
@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(1024) k_rep(const StepArgs<R> a, const Rebuild
             const bool active = t < S.ntiles && li < n;
             const int i = off + li;
             R fx = 0, fy = 0, fz = 0, u = 0, w = 0;
-            V4 ri = make_v4(R(0), R(0), R(0), R(0));
+            V4 ri{};
             int ti = 0;
             if (active) {
                 ri = s_pos[li];
@@ -284,6 +284,7 @@ __global__ void __launch_bounds__(1024) k_rep(const StepArgs<R> a, const Rebuild
                 }
             }
             merge_lanes<R, TP>(fx, fy, fz, u, w);
+            scale_force(S, fx, fy, fz);
             const bool leader = active && lt == 0;
             u *= R(0.5);
             w *= R(1.0 / 6.0);
@@ -367,9 +368,9 @@ template <typename R> __global__ void __launch_bounds__(1024) k_sort_small(const
             const int o = off + s_perm[q], d = off + q;
             a.tpos[d] = a.pos[o];
             if (!a.key_is_pos) a.tkey[d] = a.key[o];
-            a.txd[d] = a.xd[o];
-            a.tyd[d] = a.yd[o];
-            a.tzd[d] = a.zd[o];
+            a.txm[d] = a.xm[o];
+            a.tym[d] = a.ym[o];
+            a.tzm[d] = a.zm[o];
             a.tvel[d] = a.vel[o];
             a.timg[d] = a.img[o];
             a.tid[d] = s_id[s_perm[q]];

@@ -315,8 +315,9 @@ template <typename R> StepArgs<R> step_args(md_sim *s, int parity, int force_onl
     std::memset(&a, 0, sizeof(a));
     a.pos_in = (const V4 *)s->b.pos[parity];
     a.pos_out = (V4 *)s->b.pos[parity ^ 1];
-    a.xd = s->b.xd; a.yd = s->b.yd; a.zd = s->b.zd;
-    a.vel = (V4 *)s->b.vel;
+    typedef typename MT<R>::t M;
+    a.xm = (M *)s->b.xd; a.ym = (M *)s->b.yd; a.zm = (M *)s->b.zd;
+    a.vel = (typename F4T<R>::t *)s->b.vel;
     a.img = s->b.img;
     a.pos_build = (const V4 *)s->b.pos_build;
     a.nbl = s->b.nbl;
@@ -354,7 +355,7 @@ template <typename R> StepArgs<R> step_args(md_sim *s, int parity, int force_onl
     a.rebuild_batch = s->rebuild_batch;
     a.disp = s->b.disp;
     a.force_only = force_only;
-    a.f_out = (V4 *)s->b.f_out;
+    a.f_out = (typename F4T<R>::t *)s->b.f_out;
     a.w_out = (R *)s->b.w_out;
     a.has_next = 0;
     a.need_filter = -1;
@@ -371,15 +372,16 @@ template <typename R> RebuildArgs<R> rebuild_args(md_sim *s, int parity, const v
     a.pos = (V4 *)s->b.pos[parity];
     a.key = key ? (const V4 *)key : (const V4 *)s->b.pos[parity];
     a.key_is_pos = key ? 0 : 1;
-    a.xd = s->b.xd; a.yd = s->b.yd; a.zd = s->b.zd;
-    a.vel = (V4 *)s->b.vel;
+    typedef typename MT<R>::t M;
+    a.xm = (M *)s->b.xd; a.ym = (M *)s->b.yd; a.zm = (M *)s->b.zd;
+    a.vel = (typename F4T<R>::t *)s->b.vel;
     a.img = s->b.img;
     a.id = s->b.id;
     a.pos_build = (V4 *)s->b.pos_build;
     a.tpos = (V4 *)s->b.tpos;
     a.tkey = (V4 *)s->b.tkey;
-    a.txd = s->b.txd; a.tyd = s->b.tyd; a.tzd = s->b.tzd;
-    a.tvel = (V4 *)s->b.tvel;
+    a.txm = (M *)s->b.txd; a.tym = (M *)s->b.tyd; a.tzm = (M *)s->b.tzd;
+    a.tvel = (typename F4T<R>::t *)s->b.tvel;
     a.timg = s->b.timg;
     a.tid = s->b.tid;
     a.cell_of = s->b.cell_of;
@@ -647,19 +649,34 @@ template <typename R> void pack_v4(std::vector<unsigned char> &dst, size_t k, do
     std::memcpy(dst.data() + k * sizeof(v), v, sizeof(v));
 }
 
-// type word stored in .w of a position mirror
-void pack_pos(const md_sim *s, std::vector<unsigned char> &dst, size_t k, double x, double y,
-              double z, int type) {
-    if (s->precision == MD_FP64) {
-        double v[4] = {x, y, z, 0.0};
-        long long t = type;
-        std::memcpy(&v[3], &t, sizeof(double));
-        std::memcpy(dst.data() + k * 32, v, 32);
-    } else {
-        float v[4] = {(float)x, (float)y, (float)z, 0.0f};
-        std::memcpy(&v[3], &type, sizeof(float));
-        std::memcpy(dst.data() + k * 16, v, 16);
-    }
+// Mixed precision keeps positions in fixed point (the kernels' layout notes give the units):
+// master = round(x / L 2^64) of a coordinate folded into [0, L) (a value that rounds to 2^64,
+// i.e. to L, is 0), mirror = the master rounded to 32 bits.  Every step is an IEEE double
+// operation or an integer one, so both host architectures give the same bits.
+uint64_t to_fixed64(double x, double L) {
+    const double q = std::nearbyint(std::ldexp(x / L, 64));
+    if (!(q < 18446744073709551616.0)) return 0;   // 2^64: the period itself
+    return q <= 0.0 ? 0 : (uint64_t)q;
+}
+// back to a coordinate in [0, L)
+double from_fixed64(uint64_t q, double L) {
+    const double x = std::ldexp((double)q, -64) * L;
+    return x < L ? x : std::nextafter(L, 0.0);
+}
+int32_t mirror32(uint64_t q) { return (int32_t)(uint32_t)((q + 0x80000000ull) >> 32); }
+
+// FP64 mirror: x, y, z and the type's bits in .w
+void pack_pos(std::vector<unsigned char> &dst, size_t k, double x, double y, double z, int type) {
+    double v[4] = {x, y, z, 0.0};
+    long long t = type;
+    std::memcpy(&v[3], &t, sizeof(double));
+    std::memcpy(dst.data() + k * 32, v, 32);
+}
+// fixed-point mirror of a mixed-precision master position
+void pack_mirror(std::vector<unsigned char> &dst, size_t k, uint64_t qx, uint64_t qy, uint64_t qz,
+                 int type) {
+    const int32_t v[4] = {mirror32(qx), mirror32(qy), mirror32(qz), type};
+    std::memcpy(dst.data() + k * 16, v, 16);
 }
 
 void unpack_v4(const md_sim *s, const std::vector<unsigned char> &src, size_t k, double *out3) {
@@ -829,8 +846,12 @@ int md_create(md_sim **out, int n_replicas, const int *n_particles, const double
         d.invL = 1.0 / box[r];
         d.Lf = (float)box[r];
         d.invLf = (float)(1.0 / box[r]);
-        d.halfLf = (float)(0.5 * box[r]);
-        d.Llo = (float)(box[r] - (double)d.Lf);
+        d.s64 = (float)(18446744073709551616.0 / box[r]);       // 2^64 / L
+        const double unit = std::ldexp(box[r], -32);             // L / 2^32 (exact)
+        d.ps = (float)unit;
+        d.ps_lo = (float)(unit - (double)d.ps);
+        d.ps2 = (float)(unit * unit);
+        d.ps2_lo = (float)(unit * unit - (double)d.ps2);
         d.K0 = 0.5 * (3.0 * d.n - 3.0) * s->T0;
         s->off[r] = off;
         off += d.n;
@@ -992,10 +1013,19 @@ int md_set_state(md_sim *s, int r, const double *pos, const int *type, const dou
             w3[c] = v;
             im3[c] = (int)f + (image ? image[3 * k + c] : 0);
         }
-        x[k] = w3[0]; y[k] = w3[1]; z[k] = w3[2];
         img[k] = make_int4(im3[0], im3[1], im3[2], 0);
         ids[k] = k;
-        pack_pos(s, mirror, k, w3[0], w3[1], w3[2], type[k]);
+        if (s->precision == MD_FP64) {
+            x[k] = w3[0]; y[k] = w3[1]; z[k] = w3[2];
+            pack_pos(mirror, k, w3[0], w3[1], w3[2], type[k]);
+        } else {   // 64-bit fixed-point master (stored in the same 8 bytes) and its mirror
+            const uint64_t q[3] = {to_fixed64(w3[0], L), to_fixed64(w3[1], L),
+                                   to_fixed64(w3[2], L)};
+            std::memcpy(&x[k], &q[0], 8);
+            std::memcpy(&y[k], &q[1], 8);
+            std::memcpy(&z[k], &q[2], 8);
+            pack_mirror(mirror, k, q[0], q[1], q[2], type[k]);
+        }
         double vs[3];
         if (s->precision == MD_FP64) {
             pack_v4<double>(vv, k, vel[3 * k], vel[3 * k + 1], vel[3 * k + 2], 0.0);
@@ -1117,6 +1147,16 @@ int md_get_state(md_sim *s, int r, double *pos, int *image, double *vel) {
     ok = ok && cudaMemcpy(ids.data(), b.id + o, n * sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess;
     ok = ok && cudaMemcpy(vv.data(), (char *)b.vel + o * R4, n * R4, cudaMemcpyDeviceToHost) == cudaSuccess;
     if (!ok) return fail(s, MD_ECUDA);
+    if (s->precision == MD_MIXED)   // 64-bit fixed-point masters -> coordinates in [0, L)
+        for (int k = 0; k < n; ++k) {
+            uint64_t q[3];
+            std::memcpy(&q[0], &x[k], 8);
+            std::memcpy(&q[1], &y[k], 8);
+            std::memcpy(&q[2], &z[k], 8);
+            x[k] = from_fixed64(q[0], s->L[r]);
+            y[k] = from_fixed64(q[1], s->L[r]);
+            z[k] = from_fixed64(q[2], s->L[r]);
+        }
     for (int k = 0; k < n; ++k) {
         const int u = ids[k];
         if (u < 0 || u >= n) return fail(s, MD_ECUDA);
@@ -1526,7 +1566,9 @@ int md_get_log(md_sim *s, int r, int max_rows, double *out, int *rows) {
 
 // ---------------------------------------------------------------- checkpoints
 // Layout: header, then per replica: Thermo, need flag, and per particle (user order):
-// x y z (double), image (3 int), type (int), velocity (3 Real), build position (3 Real).
+// x y z (8 bytes each: the master position, double in FP64 mode, 64-bit fixed point in mixed
+// precision), image (3 int), type (int), velocity (3 Real), build position (3 x 4 bytes: the
+// 32-bit fixed-point mirror in mixed precision; 3 doubles in FP64 mode).
 namespace {
 struct CkHeader {
     char magic[8];
@@ -1577,7 +1619,7 @@ int md_save_checkpoint(md_sim *s, void *buf, size_t bytes) {
     CkHeader h;
     std::memset(&h, 0, sizeof(h));
     std::memcpy(h.magic, "MDGB300", 8);
-    h.version = 1; h.R = s->R; h.ntot = s->ntot; h.precision = s->precision; h.nt = s->nt;
+    h.version = 2; h.R = s->R; h.ntot = s->ntot; h.precision = s->precision; h.nt = s->nt;
     h.step = s->h_step;
     std::memcpy(p, &h, sizeof(h));
     p += sizeof(h);
@@ -1618,7 +1660,7 @@ int md_load_checkpoint(md_sim *s, const void *buf, size_t bytes) {
     CkHeader h;
     std::memcpy(&h, p, sizeof(h));
     p += sizeof(h);
-    if (std::memcmp(h.magic, "MDGB300", 8) != 0 || h.version != 1 || h.R != s->R ||
+    if (std::memcmp(h.magic, "MDGB300", 8) != 0 || h.version != 2 || h.R != s->R ||
         h.ntot != s->ntot || h.precision != s->precision || h.nt != s->nt)
         return MD_EINVAL;
     const size_t N = s->ntot, R4 = s->r4, rsz = R4 / 4;
@@ -1647,18 +1689,23 @@ int md_load_checkpoint(md_sim *s, const void *buf, size_t bytes) {
             types[sl] = im[3];
             if (im[3] < 0 || im[3] >= s->nt) return MD_EINVAL;
             ids[sl] = q;
-            pack_pos(s, mirror, sl, x[sl], y[sl], z[sl], types[sl]);
             std::memset(vel.data() + sl * R4, 0, R4);
             std::memcpy(vel.data() + sl * R4, d + 40, 3 * rsz);
-            double bx[3];
             if (rsz == 8) {
+                pack_pos(mirror, sl, x[sl], y[sl], z[sl], types[sl]);
+                double bx[3];
                 std::memcpy(bx, d + 40 + 3 * rsz, 24);
+                pack_pos(pb, sl, bx[0], bx[1], bx[2], types[sl]);
             } else {
-                float t3[3];
-                std::memcpy(t3, d + 40 + 3 * rsz, 12);
-                bx[0] = t3[0]; bx[1] = t3[1]; bx[2] = t3[2];
+                uint64_t qq[3];
+                std::memcpy(&qq[0], &x[sl], 8);
+                std::memcpy(&qq[1], &y[sl], 8);
+                std::memcpy(&qq[2], &z[sl], 8);
+                pack_mirror(mirror, sl, qq[0], qq[1], qq[2], types[sl]);
+                int32_t b4[4] = {0, 0, 0, types[sl]};
+                std::memcpy(b4, d + 40 + 3 * rsz, 12);
+                std::memcpy(pb.data() + sl * 16, b4, 16);
             }
-            pack_pos(s, pb, sl, bx[0], bx[1], bx[2], types[sl]);
         }
     }
     s->h_step = h.step;

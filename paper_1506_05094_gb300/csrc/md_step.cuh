@@ -34,8 +34,8 @@ template <bool NC> __device__ __forceinline__ int ld_idx(const int *p) {
 // A position half a box away from ri along x: outside every cutoff (L > 2 (range + s)), of the
 // same type, so a masked entry of the force loop contributes exact zeros.
 template <typename V4> __device__ __forceinline__ V4 far_from(const V4 &ri, const SysDesc &S);
-template <> __device__ __forceinline__ float4 far_from<float4>(const float4 &ri, const SysDesc &S) {
-    return make_float4(ri.x + S.halfLf, ri.y, ri.z, ri.w);
+template <> __device__ __forceinline__ int4 far_from<int4>(const int4 &ri, const SysDesc &) {
+    return make_int4((int)((unsigned)ri.x + 0x80000000u), ri.y, ri.z, ri.w);
 }
 template <> __device__ __forceinline__ double4_32a far_from<double4_32a>(const double4_32a &ri,
                                                                          const SysDesc &S) {
@@ -108,17 +108,15 @@ __device__ __forceinline__ void merge_lanes(R &fx, R &fy, R &fz, R &u, R &w) {
     }
 }
 
-// Leapfrog NVE / Nose-Hoover NVT update of slot i (Sec. 2), FP64 master position with image
-// counters, new FP32 mirror, skin check (Sec. 6).  Returns the particle's kinetic energy and
-// momentum.  A, B: Nose-Hoover factors (1 - xi dt/2) and 1/(1 + xi dt/2).
+// Leapfrog NVE / Nose-Hoover NVT update of slot i (Sec. 2): velocity, master position with image
+// counters, new mirror, skin check (Sec. 6).  Returns whether the particle moved more than s/2
+// since the build, its kinetic energy and momentum, and the displacement measures of the rebuild
+// slots.  A, B: Nose-Hoover factors (1 - xi dt/2) and 1/(1 + xi dt/2).
 template <typename R>
-__device__ __forceinline__ bool integrate_one(const StepArgs<R> &a, const SysDesc &S, int i,
-                                              const typename V4T<R>::t &ri, R fx, R fy, R fz,
-                                              R im, R m, R A, R B, R &ke, R &px, R &py, R &pz,
-                                              float &d2, float &st2) {
-    typedef typename V4T<R>::t V4;
+__device__ __forceinline__ void kick(const StepArgs<R> &a, int i, R fx, R fy, R fz, R im, R m,
+                                     R A, R B, typename F4T<R>::t &v, R &ke, R &px, R &py, R &pz) {
     const R dt = (R)a.dt;
-    V4 v = a.vel[i];
+    v = a.vel[i];
     if (a.integrator == 1) {
         v.x = (A * v.x + dt * fx * im) * B;
         v.y = (A * v.y + dt * fy * im) * B;
@@ -133,43 +131,92 @@ __device__ __forceinline__ bool integrate_one(const StepArgs<R> &a, const SysDes
     px = m * v.x;
     py = m * v.y;
     pz = m * v.z;
-    // FP64 master position, wrap and image (the mixed-precision contract).  The wrap is detected
-    // on the rounded mirror (it can only round up to L, never below 0) and decided exactly in FP64
-    // only when the mirror says the particle may have left [0, L).
-    double x = a.xd[i] + (double)(dt * v.x), y = a.yd[i] + (double)(dt * v.y),
-           z = a.zd[i] + (double)(dt * v.z);
-    const R Lr = box_L<R>(S);
-    int wx = 0, wy = 0, wz = 0;
-    if (!((R)x < Lr && (R)x >= R(0))) {
-        if (x >= S.L) { x -= S.L; wx = 1; } else if (x < 0.0) { x += S.L; wx = -1; }
+}
+
+// runaway / non-finite displacement (more than L/4 in one step): halt
+__device__ __forceinline__ void check_runaway(const Ctrl *c, bool ok) {
+    if (!ok) {
+        atomicExch((int *)&c->unstable, 1);
+        atomicExch((int *)&c->halt, 1);
     }
-    if (!((R)y < Lr && (R)y >= R(0))) {
-        if (y >= S.L) { y -= S.L; wy = 1; } else if (y < 0.0) { y += S.L; wy = -1; }
-    }
-    if (!((R)z < Lr && (R)z >= R(0))) {
-        if (z >= S.L) { z -= S.L; wz = 1; } else if (z < 0.0) { z += S.L; wz = -1; }
-    }
-    a.xd[i] = x;
-    a.yd[i] = y;
-    a.zd[i] = z;
+}
+
+// Mixed precision: the master position is 64-bit fixed point (2^64 units per period).  The
+// FP32 displacement dt v is converted to those units (one rounding, 2^-24 relative, the FP32
+// precision of v itself) and added as an integer: the add is exact, and a carry out of 64 bits is
+// exactly a crossing of the box face, which moves the image counter.  The mirror is the master
+// rounded to 32 bits.  No FP64 instruction.
+__device__ __forceinline__ bool integrate_one(const StepArgs<float> &a, const SysDesc &S, int i,
+                                              const int4 &ri, float fx, float fy, float fz,
+                                              float im, float m, float A, float B, float &ke,
+                                              float &px, float &py, float &pz, float &d2,
+                                              float &st2) {
+    float4 v;
+    kick(a, i, fx, fy, fz, im, m, A, B, v, ke, px, py, pz);
+    const float dt = (float)a.dt;
+    const float ex = dt * v.x, ey = dt * v.y, ez = dt * v.z;
+    const float lim = 0.25f * S.Lf;
+    check_runaway(a.ctrl, fabsf(ex) < lim && fabsf(ey) < lim && fabsf(ez) < lim);
+    const long long qx = __float2ll_rn(ex * S.s64), qy = __float2ll_rn(ey * S.s64),
+                    qz = __float2ll_rn(ez * S.s64);
+    const unsigned long long ox = a.xm[i], oy = a.ym[i], oz = a.zm[i];
+    const unsigned long long nx = ox + (unsigned long long)qx, ny = oy + (unsigned long long)qy,
+                             nz = oz + (unsigned long long)qz;
+    a.xm[i] = nx;
+    a.ym[i] = ny;
+    a.zm[i] = nz;
+    // a wrap of the unsigned add is a crossing of the face at 0 == L
+    const int wx = qx > 0 ? (nx < ox) : -(int)(nx > ox);
+    const int wy = qy > 0 ? (ny < oy) : -(int)(ny > oy);
+    const int wz = qz > 0 ? (nz < oz) : -(int)(nz > oz);
     if (wx | wy | wz) {
         int4 g = a.img[i];
         g.x += wx; g.y += wy; g.z += wz;
         a.img[i] = g;
     }
-    const R lim = (R)(0.25 * S.L);   // runaway / non-finite displacement
-    if (!(fabs(dt * v.x) < lim && fabs(dt * v.y) < lim && fabs(dt * v.z) < lim)) {
-        atomicExch(&a.ctrl->unstable, 1);
-        atomicExch(&a.ctrl->halt, 1);
-    }
-    const V4 rn = make_v4((R)x, (R)y, (R)z, ri.w);
+    const int4 rn = make_int4((int)((nx + 0x80000000ull) >> 32), (int)((ny + 0x80000000ull) >> 32),
+                              (int)((nz + 0x80000000ull) >> 32), ri.w);
     a.pos_out[i] = rn;
-    const V4 pb = a.pos_build[i];
-    const R L = box_L<R>(S), invL = box_invL<R>(S);
-    const R bx = min_image_fast(rn.x - pb.x, L, invL);
-    const R by = min_image_fast(rn.y - pb.y, L, invL);
-    const R bz = min_image_fast(rn.z - pb.z, L, invL);
-    const R db2 = bx * bx + by * by + bz * bz;
+    const int4 pb = a.pos_build[i];
+    const float bx = fixed_diff(rn.x, pb.x), by = fixed_diff(rn.y, pb.y), bz = fixed_diff(rn.z, pb.z);
+    const float b2 = bx * bx + by * by + bz * bz;
+    const float db2 = __fmaf_rn(b2, S.ps2, b2 * S.ps2_lo);
+    d2 = db2;
+    st2 = ex * ex + ey * ey + ez * ez;
+    return db2 > a.half_skin2;
+}
+
+// FP64: the master position is a double; the wrap is decided exactly in FP64.
+__device__ __forceinline__ bool integrate_one(const StepArgs<double> &a, const SysDesc &S, int i,
+                                              const double4_32a &ri, double fx, double fy,
+                                              double fz, double im, double m, double A, double B,
+                                              double &ke, double &px, double &py, double &pz,
+                                              float &d2, float &st2) {
+    double4_32a v;
+    kick(a, i, fx, fy, fz, im, m, A, B, v, ke, px, py, pz);
+    const double dt = a.dt;
+    double x = a.xm[i] + dt * v.x, y = a.ym[i] + dt * v.y, z = a.zm[i] + dt * v.z;
+    int wx = 0, wy = 0, wz = 0;
+    if (x >= S.L) { x -= S.L; wx = 1; } else if (x < 0.0) { x += S.L; wx = -1; }
+    if (y >= S.L) { y -= S.L; wy = 1; } else if (y < 0.0) { y += S.L; wy = -1; }
+    if (z >= S.L) { z -= S.L; wz = 1; } else if (z < 0.0) { z += S.L; wz = -1; }
+    a.xm[i] = x;
+    a.ym[i] = y;
+    a.zm[i] = z;
+    if (wx | wy | wz) {
+        int4 g = a.img[i];
+        g.x += wx; g.y += wy; g.z += wz;
+        a.img[i] = g;
+    }
+    const double lim = 0.25 * S.L;
+    check_runaway(a.ctrl, fabs(dt * v.x) < lim && fabs(dt * v.y) < lim && fabs(dt * v.z) < lim);
+    const double4_32a rn = make_double4_32a(x, y, z, ri.w);
+    a.pos_out[i] = rn;
+    const double4_32a pb = a.pos_build[i];
+    const double bx = min_image_fast(rn.x - pb.x, S.L, S.invL);
+    const double by = min_image_fast(rn.y - pb.y, S.L, S.invL);
+    const double bz = min_image_fast(rn.z - pb.z, S.L, S.invL);
+    const double db2 = bx * bx + by * by + bz * bz;
     d2 = (float)db2;
     st2 = (float)(dt * dt * (v.x * v.x + v.y * v.y + v.z * v.z));
     return db2 > a.half_skin2;
@@ -437,7 +484,7 @@ __global__ void __launch_bounds__(1024) k_step(const StepArgs<R> a) {
     const int i = S.off + li;
 
     R fx = 0, fy = 0, fz = 0, u = 0, w = 0;
-    V4 ri = make_v4(R(0), R(0), R(0), R(0));
+    V4 ri{};
     int ti = 0;
     if (active) {
         ri = STAGE ? s_pos[li] : a.pos_in[i];
@@ -458,6 +505,7 @@ __global__ void __launch_bounds__(1024) k_step(const StepArgs<R> a) {
         }
     }
     merge_lanes<R, TP>(fx, fy, fz, u, w);
+    scale_force(S, fx, fy, fz);
     const bool leader = active && lt == 0;
     u *= R(0.5);          // Fig. 2: compensate the double counting of the full list
     w *= R(1.0 / 6.0);    // 1/2 (double counting) * 1/3 (virial)

@@ -5,8 +5,25 @@ import synth
 
 
 def f32(a):
-    """Round to FP32 and back: the values the mixed-precision device path actually holds."""
+    """Round to FP32 and back: the values the mixed-precision device path holds for velocities
+    (and the allocation-free entry point for positions)."""
     return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def dev_pos(pos, L):
+    """The positions the mixed-precision device computes with: its fixed-point mirror
+    (oracle.device_grid), as FP64 values on the 2^-32 L grid.  For positions read back after
+    steps (md_get_state returns the 64-bit master) this is the mirror to within one grid unit."""
+    import oracle
+
+    return oracle.device_grid(pos, L)[1]
+
+
+def dev_q(pos, L):
+    """The fixed-point mirror itself (uint32 (n,3)) for the bit-defined list rule."""
+    import oracle
+
+    return oracle.device_grid(pos, L)[0]
 
 
 def rel_rms(a, b):

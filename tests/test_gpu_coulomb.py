@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import f32, make_sim, rel_rms
+from gpu_util import f32, make_sim, rel_rms, dev_pos, dev_q
 
 pytestmark = pytest.mark.gpu
 
@@ -33,7 +33,7 @@ def _salt(n, seed=21):
 def _check(sim, st, model, cutoff="sp", tol=1e-5, utol=1e-6):
     f, u, w = sim.forces(0)
     with oracle.cutoff(cutoff):
-        fr, ur, wr, U, W = oracle.forces(f32(st.pos), st.types, st.L, model)
+        fr, ur, wr, U, W = oracle.forces(dev_pos(st.pos, st.L), st.types, st.L, model)
     assert rel_rms(f, fr) <= tol, rel_rms(f, fr)
     assert abs(u.sum() - U) <= utol * np.abs(ur).sum(), (u.sum(), U)
     assert abs(w.sum() - W) <= utol * np.abs(wr).sum(), (w.sum(), W)
@@ -66,7 +66,7 @@ def test_salt_pair_sets_bit_exact_with_the_coulomb_range():
     with make_sim(SALT, [st]) as sim:
         sim.forces(0)
         counts, nb = sim.neighbors(0)
-    ref, rc = oracle.neighbors_fp32(f32(st.pos), st.types, st.L, SALT, 0.3)
+    ref, rc = oracle.neighbors_fixed(dev_q(st.pos, st.L), st.types, st.L, SALT, 0.3)
     np.testing.assert_array_equal(counts, rc)
     for i in range(st.n):
         np.testing.assert_array_equal(np.sort(nb[i, :counts[i]]), ref[i])
@@ -87,7 +87,7 @@ def test_salt_large_sampled():
     with make_sim(SALT, [st]) as sim:
         f, u, w = sim.forces(0)
     idx = np.random.default_rng(3).choice(st.n, 64, replace=False)
-    fr, ur, wr = oracle.forces_subset(f32(st.pos), st.types, st.L, SALT, idx)
+    fr, ur, wr = oracle.forces_subset(dev_pos(st.pos, st.L), st.types, st.L, SALT, idx)
     assert rel_rms(f[idx], fr) < 1e-5
     np.testing.assert_allclose(u[idx], ur, rtol=0, atol=1e-5 * np.abs(ur).max())
 

@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import f32, ka, make_sim, rel_rms
+from gpu_util import f32, ka, make_sim, rel_rms, dev_pos, dev_q
 
 pytestmark = pytest.mark.gpu
 
@@ -34,7 +34,11 @@ def test_unwrapped_and_boundary_coordinates():
     g = np.arange(k) * (L / k)
     lat = np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1).reshape(-1, 3)
     rng = np.random.default_rng(5)
-    raw = lat + L * rng.integers(-3, 4, size=lat.shape)
+    # a small jitter off the lattice planes away from 0 (a perfect lattice would make the FP32
+    # rounding of equal pair distances add up coherently); the coordinates on the plane at 0
+    # become the boundary values below
+    jit = np.where(lat == 0.0, 0.0, rng.uniform(-0.05, 0.05, lat.shape))
+    raw = lat + jit + L * rng.integers(-3, 4, size=lat.shape)
     zero = np.argwhere(lat == 0.0)
     for m, (i, c) in enumerate(zero[:60]):
         raw[i, c] = L if m % 2 == 0 else -1e-13
@@ -46,7 +50,7 @@ def test_unwrapped_and_boundary_coordinates():
         assert np.all(pos >= 0.0) and np.all(pos < L)
         np.testing.assert_allclose(pos + img * L, raw, rtol=0, atol=1e-12 * L * 8)
         f, u, w = sim.forces(0)
-    fr, ur, wr, U, W = oracle.forces(f32(pos), types, L, KA)
+    fr, ur, wr, U, W = oracle.forces(dev_pos(pos, L), types, L, KA)
     assert rel_rms(f, fr) <= 1e-5
     assert abs(u.sum() - U) <= 1e-6 * abs(U)
 
@@ -60,7 +64,7 @@ def test_two_particle_replica_beside_a_large_one():
     with make_sim(KA, [two, big], integrator="nve", dt=0.0025, graph_block=10) as sim:
         for r, st in enumerate([two, big]):
             f, u, w = sim.forces(r)
-            fr, ur, wr, U, W = oracle.forces(f32(st.pos), st.types, st.L, KA)
+            fr, ur, wr, U, W = oracle.forces(dev_pos(st.pos, st.L), st.types, st.L, KA)
             assert rel_rms(f, fr) <= 1e-5
             assert abs(u.sum() - U) <= 1e-6 * abs(U)
         sim.step(50)
@@ -84,11 +88,11 @@ def test_smallest_box_and_the_rejected_one():
     with make_sim(KA, [st]) as sim:
         f, u, w = sim.forces(0)
         counts, nb = sim.neighbors(0)
-    ref, rc = oracle.neighbors_fp32(f32(st.pos), st.types, st.L, KA, 0.3)
+    ref, rc = oracle.neighbors_fixed(dev_q(st.pos, st.L), st.types, st.L, KA, 0.3)
     np.testing.assert_array_equal(counts, rc)
     for i in range(st.n):
         np.testing.assert_array_equal(np.sort(nb[i, :counts[i]]), ref[i])
-    fr = oracle.forces(f32(st.pos), st.types, st.L, KA)[0]
+    fr = oracle.forces(dev_pos(st.pos, st.L), st.types, st.L, KA)[0]
     assert rel_rms(f, fr) <= 1e-5
     with pytest.raises(MDError) as ex:
         Sim([n], [lim - 1e-6], KA.eps, KA.sigma, KA.rc, KA.mass, skin=0.3)
@@ -107,7 +111,7 @@ def test_million_particle_system_sampled():
         pos, _, _ = sim.get_state(0)
         f, u, w = sim.forces(0)
     idx = np.random.default_rng(4).choice(st.n, 64, replace=False)
-    fr, ur, wr = oracle.forces_subset(f32(pos), st.types, st.L, LJ, idx)
+    fr, ur, wr = oracle.forces_subset(dev_pos(pos, st.L), st.types, st.L, LJ, idx)
     assert rel_rms(f[idx], fr) < 1e-5
     np.testing.assert_allclose(u[idx], ur, rtol=0, atol=1e-5 * np.abs(ur).max())
     H, U = lg[:, 7], lg[:, 1]           # leaving the lattice moves U fast; H stays put

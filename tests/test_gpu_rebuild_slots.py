@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import f32, ka, make_sim, rel_rms
+from gpu_util import f32, ka, make_sim, rel_rms, dev_pos
 
 pytestmark = pytest.mark.gpu
 
@@ -55,7 +55,7 @@ def test_slots_gather_rebuild_passes_and_keep_lists_valid():
     assert s4["replica_rebuilds"] < 1.5 * s1["replica_rebuilds"]
     for r, st in enumerate(sts):              # forces at the final positions: list still valid
         f, u, w = forces[r]
-        fr, ur, wr, U, W = oracle.forces(f32(out[r][0]), st.types, st.L, KA)
+        fr, ur, wr, U, W = oracle.forces(dev_pos(out[r][0], st.L), st.types, st.L, KA)
         assert rel_rms(f, fr) <= 1e-5
         assert abs(u.sum() - U) <= 1e-6 * abs(U)
 

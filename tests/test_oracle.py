@@ -201,21 +201,48 @@ def test_neighbors_match_image_enumeration():
     assert all((j, i) in pairs for (i, j) in pairs)
 
 
-def test_neighbors_fp32_agree_with_fp64_away_from_threshold():
+def test_neighbors_fixed_agree_with_fp64_away_from_threshold():
+    """The fixed-point list rule (the mixed-precision mirror) gives the FP64 brute-force sets of
+    the same grid positions, except for pairs within 1e-5 relative of the threshold."""
     s = synth.ka_random_state(1000, 1.2, 1.0, 9)
-    posf = s.pos.astype(np.float32)
-    n64, _ = oracle.neighbors_fp64(posf.astype(np.float64), s.types, s.L, KA, 0.3)
-    n32, _ = oracle.neighbors_fp32(posf, s.types, s.L, KA, 0.3)
+    q, xg = oracle.device_grid(s.pos, s.L)
+    n64, _ = oracle.neighbors_fp64(xg, s.types, s.L, KA, 0.3)
+    nfx, _ = oracle.neighbors_fixed(q, s.types, s.L, KA, 0.3)
     near = 0
     for i in range(s.n):
-        a, b = set(n64[i].tolist()), set(n32[i].tolist())
+        a, b = set(n64[i].tolist()), set(nfx[i].tolist())
         for j in a ^ b:
-            d = posf[j].astype(np.float64) - posf[i]
+            d = xg[j] - xg[i]
             d -= s.L * np.round(d / s.L)
             thr = (KA.rc[s.types[i], s.types[j]] + 0.3) ** 2
             assert abs(d @ d - thr) < 1e-5 * thr
             near += 1
     assert near < 10
+
+
+def test_device_grid_folds_rounds_and_wraps():
+    """The device's fixed-point image: grid values q L / 2^32 within half a unit of the folded
+    coordinate; the face at L, -tiny and whole periods fold onto the grid like [0, L) values;
+    the 32-bit difference of two mirrors is the nearest periodic image of their distance."""
+    L = 13.7
+    rng = np.random.default_rng(3)
+    x = rng.uniform(0, L, (500, 3))
+    q, xg = oracle.device_grid(x, L)
+    unit = math.ldexp(L, -32)
+    np.testing.assert_array_equal(xg, q.astype(np.float64) * unit)
+    assert np.all(np.abs(xg - x) <= 0.5 * unit * (1 + 1e-9) + 1e-15)
+    # whole periods and the faces
+    q2, _ = oracle.device_grid(x + L * rng.integers(-3, 4, x.shape), L)
+    dq = ((q2.astype(np.int64) - q.astype(np.int64) + 2 ** 31) % 2 ** 32) - 2 ** 31
+    assert np.all(np.abs(dq) <= 1)      # the FP64 fold of x + k L rounds to within one unit
+    qs, xs = oracle.device_grid(np.array([[L, -1e-17, 0.0], [L - 1e-15, 2 * L, -L]]), L)
+    np.testing.assert_array_equal(qs, 0)
+    # nearest image from the 32-bit difference
+    i, j = rng.integers(0, 500, 200), rng.integers(0, 500, 200)
+    d32 = ((q[j].astype(np.int64) - q[i].astype(np.int64) + 2 ** 31) % 2 ** 32) - 2 ** 31
+    d64 = xg[j] - xg[i]
+    d64 -= L * np.round(d64 / L)
+    np.testing.assert_allclose(d32 * unit, d64, rtol=0, atol=1e-12 * L)
 
 
 # --------------------------------------------------------------------------------------------
