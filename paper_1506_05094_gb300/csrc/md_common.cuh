@@ -237,7 +237,7 @@ __device__ __forceinline__ void interact(const typename V4T<R>::t &ri, int ti,
             p = ti * nt + type_of(rj);
             c = s_c0[p];
         }
-        const bool in = r2 < c.x;
+        const bool in = r2 < c.x && r2 > R(0);   // r2 = 0: a pad entry (the particle itself)
         const R r2i = fast_rcp(r2);
         const R r6i = r2i * r2i * r2i;
         const R t = c.y * r6i - c.z;                    // c12 r^-6 - c6
@@ -253,7 +253,7 @@ __device__ __forceinline__ void interact(const typename V4T<R>::t &ri, int ti,
         u += in ? uu : R(0);
         if (POT & 2) {
             const typename Coef4<R>::t q = s_cq[p];
-            const bool inq = r2 < q.x;
+            const bool inq = r2 < q.x && r2 > R(0);
             const R rinv = fast_rsqrt(r2);
             const R fq = rinv * (q.y * rinv * rinv - q.z);
             const R uq = q.y * rinv - q.w + q.z * (r2 * rinv);
@@ -266,6 +266,7 @@ __device__ __forceinline__ void interact(const typename V4T<R>::t &ri, int ti,
         w += fs * r2;
         return;
     }
+    if (!(r2 > R(0))) return;   // a pad entry (the particle itself)
     if (SINGLE) {
         if (r2 < c1.x) lj_pair<SF>(dx, dy, dz, r2, c1, c1b, fx, fy, fz, u, w);
     } else {

@@ -186,6 +186,8 @@ template <typename R> struct RebuildArgs {
     int *plan_rep, *plan_pp, *plan_pc;
     int nsm;                 // SMs, for the persistent grids
     int tpb;                 // lanes per particle in the list build
+    int pad;                 // lists are padded with the particle's own slot to a multiple of this
+                             // (4 x the step kernel's threads per particle; n_max is a multiple)
     int sort_small;          // 1: one-CTA-per-replica fused sort (k_sort_small)
     int sort_nmax, sort_cmax;
     size_t sort_smem;

@@ -363,6 +363,16 @@ __device__ __forceinline__ int build_one(const SysDesc &S, const KeySrc &K, cons
     return cnt;
 }
 
+// Pad a list of cnt entries with the particle's own slot up to the next multiple of `pad`
+// (4 x the step kernel's threads per particle, and n_max is a multiple of it), so every lane of
+// the force loop runs whole groups of four entries with no bounds test; a padded entry is the
+// particle itself, at distance 0, which the pair arithmetic excludes.  TPB lanes share the work.
+__device__ __forceinline__ void pad_list(int *nbl, int slot_i, int cnt, int nmax, int pad, int lt,
+                                         int TPB) {
+    const int end = min(nmax, (cnt + pad - 1) / pad * pad);
+    for (int k = cnt + lt; k < end; k += TPB) nbl[nbl_offset(slot_i, k, nmax)] = slot_i;
+}
+
 template <typename R> struct GlobalKey {
     const typename V4T<R>::t *p;
     __device__ __forceinline__ typename V4T<R>::t operator()(int j) const { return p[j]; }
@@ -377,7 +387,7 @@ struct GlobalStart {   // cell starts of replica S in the global cellStart array
 #define MD_MAX_RANGES 98
 #define MD_BUILD_BLOCK 128
 
-template <typename R, int TPB> __global__ void __launch_bounds__(MD_BUILD_BLOCK) k_build(const RebuildArgs<R> a) {
+template <typename R, int TPB> __global__ void __launch_bounds__(MD_BUILD_BLOCK, 12) k_build(const RebuildArgs<R> a) {
     typedef typename V4T<R>::t V4;
     if (cells_off(a)) return;
     __shared__ R s_thr[MD_MAX_PAIRS];
@@ -397,6 +407,7 @@ template <typename R, int TPB> __global__ void __launch_bounds__(MD_BUILD_BLOCK)
         GlobalStart CS{a.cell_start, S.cell_off};
         int cnt = build_one<R, TPB, true>(S, K, CS, i, i, 0, a.nbl, a.nmax, s_thr, a.ntypes,
                                           s_rng_all[threadIdx.x / TPB]);
+        pad_list(a.nbl, i, cnt, a.nmax, a.pad, threadIdx.x % TPB, TPB);
         if (threadIdx.x % TPB == 0) {
             if (cnt > a.nmax) {   // Sec. 4: out of space -> flag for the host, which doubles n_max
                 atomicMax(&a.ctrl->max_count, cnt);
@@ -456,6 +467,7 @@ __global__ void __launch_bounds__(MD_BUILD_BLOCK) k_build_n2(const RebuildArgs<R
             }
             cnt += __popc(m);
         }
+        pad_list(a.nbl, i, cnt, a.nmax, a.pad, lt, TPB);
         if (lt == 0) {
             if (cnt > a.nmax) {
                 atomicMax(&a.ctrl->max_count, cnt);

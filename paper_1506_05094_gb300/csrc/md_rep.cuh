@@ -154,6 +154,7 @@ __device__ __forceinline__ int cta_rebuild(const RebuildArgs<R> &b, const SysDes
     for (int g = threadIdx.x / TPB; g < n; g += blockDim.x / TPB) {
         int cnt = build_one<R, TPB, false>(S, K, CS, g, off + g, off, b.nbl, b.nmax, s_thr,
                                            b.ntypes, nullptr);
+        pad_list(b.nbl, off + g, cnt, b.nmax, b.pad, threadIdx.x % TPB, TPB);
         if (threadIdx.x % TPB == 0) {
             if (cnt > b.nmax) {
                 atomicMax(&b.ctrl->max_count, cnt);
@@ -277,7 +278,7 @@ __global__ void __launch_bounds__(1024) k_rep(const StepArgs<R> a, const Rebuild
                 if (!direct) {
                     SharedPos<R> src{s_pos, off};
                     force_sum<R, TP, SINGLE, SharedPos<R>, false>(a, src, i, ri, ti, F, lt, s_c0,
-                                                                 s_c1, fx, fy, fz, u, w, nullptr, &S);
+                                                                 s_c1, fx, fy, fz, u, w);
                 } else {
                     force_direct<R, TP, SINGLE>(a, S, s_pos, s_cs, li, ri, ti, F, lt, s_c0, s_c1,
                                                 fx, fy, fz, u, w);

@@ -271,6 +271,14 @@ int configure_layout(md_sim *s, bool realloc_cells) {
     return MD_OK;
 }
 
+// Lists are padded to a multiple of 4 x tp entries (the force loop's groups of four per lane), and
+// the capacity n_max is kept a multiple of that.
+int list_pad(const md_sim *s) { return 4 * s->tp; }
+int round_nmax(const md_sim *s, int n) {
+    const int p = list_pad(s);
+    return (n + p - 1) / p * p;
+}
+
 // sliced layout: ceil(ntot / 32) slices of nmax x 32 entries
 size_t nbl_entries(const md_sim *s) { return (((size_t)s->ntot + 31) / 32) * 32 * (size_t)s->nmax; }
 
@@ -400,6 +408,7 @@ template <typename R> RebuildArgs<R> rebuild_args(md_sim *s, int parity, const v
     a.plan_pc = s->b.plan_arr + 2 * s->R + 1;
     a.nsm = s->nsm;
     a.tpb = s->tpb;
+    a.pad = list_pad(s);
     a.sort_small = s->sort_small ? 1 : 0;
     a.list_method = s->list_method == 1 ? 1 : 0;
     a.resort = s->list_method == 1 ? s->resort : 0;
@@ -587,7 +596,7 @@ int read_ctrl(md_sim *s) {
 int recover_overflow(md_sim *s) {
     const int seen = s->h_ctrl->max_count;
     int nm = std::max(2 * s->nmax, seen + seen / 4 + 8);
-    s->nmax = nm;
+    s->nmax = round_nmax(s, nm);
     destroy_graphs(s);
     if (alloc_nbl(s)) return MD_ENOMEM;
     Ctrl c = *s->h_ctrl;
@@ -606,7 +615,7 @@ int recover_overflow(md_sim *s) {
 
 int grow_after_rep_overflow(md_sim *s) {
     const int seen = s->h_ctrl->max_count;
-    s->nmax = std::max(2 * s->nmax, seen + seen / 4 + 8);
+    s->nmax = round_nmax(s, std::max(2 * s->nmax, seen + seen / 4 + 8));
     destroy_graphs(s);
     if (alloc_nbl(s)) return MD_ENOMEM;
     Ctrl c = *s->h_ctrl;
@@ -861,8 +870,8 @@ int md_create(md_sim **out, int n_replicas, const int *n_particles, const double
         n_big = std::max(n_big, d.n);
     }
     // Sec. 4: fixed-capacity list; start with headroom and grow x2 on overflow
-    s->nmax = estimate_nmax(s);
     s->tp = 1;
+    s->nmax = round_nmax(s, estimate_nmax(s));
     s->block = 128;
     s->reach = 2;
 
@@ -1286,14 +1295,19 @@ int md_set_tuning(md_sim *s, int tp, int block, int reach, int build_lanes) {
         return MD_EINVAL;
     if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(s, MD_ECUDA);
     const bool cells_change = nr != s->reach;
+    const bool pad_change = ntp != s->tp;   // lists are padded for the force loop's tp
     s->tp = ntp;
     s->block = nb;
     s->reach = nr;
     s->tpb = nl;
     destroy_graphs(s);
+    if (pad_change && round_nmax(s, s->nmax) != s->nmax) {
+        s->nmax = round_nmax(s, s->nmax);
+        if (alloc_nbl(s)) return MD_ENOMEM;
+    }
     int rc = configure_layout(s, cells_change);
     if (rc) return rc == MD_ENOMEM ? MD_ENOMEM : fail(s, MD_ECUDA);
-    if (cells_change) return request_rebuild_all(s);
+    if (cells_change || pad_change) return request_rebuild_all(s);
     return MD_OK;
 }
 
@@ -1346,7 +1360,7 @@ int md_set_coulomb(md_sim *s, const double *charge, double rc_coulomb) {
             t.qrc2 = (float)t.qrc2d; t.qq = (float)t.qqd; t.qf = (float)t.qfd; t.qu = (float)t.qud;
         }
     if (upload_thresholds(s)) return fail(s, MD_ECUDA);
-    const int need = estimate_nmax(s);
+    const int need = round_nmax(s, estimate_nmax(s));
     if (need > s->nmax) {
         s->nmax = need;
         if (alloc_nbl(s)) return MD_ENOMEM;
@@ -1383,7 +1397,7 @@ int md_set_skin(md_sim *s, double skin) {
     destroy_graphs(s);
     s->skin = skin;
     if (upload_thresholds(s)) return fail(s, MD_ECUDA);
-    const int need = estimate_nmax(s);
+    const int need = round_nmax(s, estimate_nmax(s));
     if (need > s->nmax) {
         s->nmax = need;
         if (alloc_nbl(s)) return MD_ENOMEM;
@@ -1404,7 +1418,7 @@ int md_set_list_capacity(md_sim *s, int n_max) {
     if (s->sticky) return s->sticky;
     if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(s, MD_ECUDA);
     destroy_graphs(s);
-    s->nmax = n_max;
+    s->nmax = round_nmax(s, n_max);
     if (alloc_nbl(s)) return MD_ENOMEM;
     return request_rebuild_all(s);
 }

@@ -31,45 +31,35 @@ template <bool NC> __device__ __forceinline__ int ld_idx(const int *p) {
 
 // NC: the list may be read through the non-coherent read-only path (it was written by an
 // earlier kernel); false when the same kernel has just built it.
-// A position half a box away from ri along x: outside every cutoff (L > 2 (range + s)), of the
-// same type, so a masked entry of the force loop contributes exact zeros.
-template <typename V4> __device__ __forceinline__ V4 far_from(const V4 &ri, const SysDesc &S);
-template <> __device__ __forceinline__ int4 far_from<int4>(const int4 &ri, const SysDesc &) {
-    return make_int4((int)((unsigned)ri.x + 0x80000000u), ri.y, ri.z, ri.w);
-}
-template <> __device__ __forceinline__ double4_32a far_from<double4_32a>(const double4_32a &ri,
-                                                                         const SysDesc &S) {
-    return make_double4_32a(ri.x + 0.5 * S.L, ri.y, ri.z, ri.w);
-}
 template <typename R, int TP, bool SINGLE, typename Src, bool NC = true, int SF = 0>
 __device__ __forceinline__ void force_sum(const StepArgs<R> &a, const Src &P4, int i,
                                           const typename V4T<R>::t &ri, int ti, const Frame<R> &F,
                                           int lt, const typename Coef4<R>::t *s_c0,
                                           const typename Coef4<R>::t *s_c1, R &fx, R &fy, R &fz,
                                           R &u, R &w,
-                                          const typename Coef4<R>::t *s_cq = nullptr,
-                                          const SysDesc *Sp = nullptr) {
+                                          const typename Coef4<R>::t *s_cq = nullptr) {
     typedef typename V4T<R>::t V4;
     const typename Coef4<R>::t c1 = s_c0[0];
     const typename Coef4<R>::t c1b = s_c1[0];
     const int nn = a.nnb[i];
-    const int m = nn > lt ? (nn - lt + TP - 1) / TP : 0;   // entries of this lane
+    // entries of this lane, rounded up to whole groups of four: the list is padded with the
+    // particle's own slot (pad_list), so every index read is a valid entry and no lane tests bounds
+    const int m = ((nn > lt ? (nn - lt + TP - 1) / TP : 0) + 3) & ~3;
     const int stride = TP * 32;
     const int *q = a.nbl + nbl_offset(i, lt, a.nmax);
-    const V4 far = far_from(ri, *Sp);
-    // groups of four entries, the indices of the next group loaded while this one is evaluated;
-    // entries past the end of the lane's list read the far position instead (no remainder loop:
-    // a lane's last, partial group costs one pass of the loop, not up to three dependent ones)
-    int j0 = 0 < m ? ld_idx<NC>(q) : -1, j1 = 1 < m ? ld_idx<NC>(q + stride) : -1;
-    int j2 = 2 < m ? ld_idx<NC>(q + 2 * stride) : -1, j3 = 3 < m ? ld_idx<NC>(q + 3 * stride) : -1;
+    // groups of four entries, the indices of the next group loaded while this one is evaluated
+    int j0 = 0, j1 = 0, j2 = 0, j3 = 0;
+    if (m > 0) {
+        j0 = ld_idx<NC>(q); j1 = ld_idx<NC>(q + stride); j2 = ld_idx<NC>(q + 2 * stride);
+        j3 = ld_idx<NC>(q + 3 * stride);
+    }
     for (int e = 0; e < m; e += 4) {
-        const V4 r0 = j0 >= 0 ? P4(j0) : far, r1 = j1 >= 0 ? P4(j1) : far;
-        const V4 r2 = j2 >= 0 ? P4(j2) : far, r3 = j3 >= 0 ? P4(j3) : far;
+        const V4 r0 = P4(j0), r1 = P4(j1), r2 = P4(j2), r3 = P4(j3);
         q += 4 * stride;
-        j0 = e + 4 < m ? ld_idx<NC>(q) : -1;
-        j1 = e + 5 < m ? ld_idx<NC>(q + stride) : -1;
-        j2 = e + 6 < m ? ld_idx<NC>(q + 2 * stride) : -1;
-        j3 = e + 7 < m ? ld_idx<NC>(q + 3 * stride) : -1;
+        if (e + 4 < m) {   // prefetch the next four indices (Sec. 5 prefetching)
+            j0 = ld_idx<NC>(q); j1 = ld_idx<NC>(q + stride); j2 = ld_idx<NC>(q + 2 * stride);
+            j3 = ld_idx<NC>(q + 3 * stride);
+        }
         interact<R, SINGLE, SF>(ri, ti, r0, F, a.ntypes, s_c0, s_c1, c1, c1b, fx, fy, fz, u, w, s_cq);
         interact<R, SINGLE, SF>(ri, ti, r1, F, a.ntypes, s_c0, s_c1, c1, c1b, fx, fy, fz, u, w, s_cq);
         interact<R, SINGLE, SF>(ri, ti, r2, F, a.ntypes, s_c0, s_c1, c1, c1b, fx, fy, fz, u, w, s_cq);
@@ -493,7 +483,7 @@ __global__ void __launch_bounds__(1024) k_step(const StepArgs<R> a) {
         if (STAGE) {
             SharedPos<R> src{s_pos, S.off};
             force_sum<R, TP, SINGLE, SharedPos<R>, true, SF>(a, src, i, ri, ti, F, lt, s_c0, s_c1,
-                                                             fx, fy, fz, u, w, s_cq, &S);
+                                                             fx, fy, fz, u, w, s_cq);
         } else if (a.nolist) {
             GlobalPos<R> src{a.pos_in};
             force_all<R, TP, SINGLE, SF>(a, src, S, i, ri, ti, F, lt, s_c0, s_c1, fx, fy, fz, u, w,
@@ -501,7 +491,7 @@ __global__ void __launch_bounds__(1024) k_step(const StepArgs<R> a) {
         } else {
             GlobalPos<R> src{a.pos_in};
             force_sum<R, TP, SINGLE, GlobalPos<R>, true, SF>(a, src, i, ri, ti, F, lt, s_c0, s_c1,
-                                                             fx, fy, fz, u, w, s_cq, &S);
+                                                             fx, fy, fz, u, w, s_cq);
         }
     }
     merge_lanes<R, TP>(fx, fy, fz, u, w);
