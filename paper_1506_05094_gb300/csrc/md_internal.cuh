@@ -82,6 +82,9 @@ struct PairTab {
 struct Thermo {
     double xi_prev;   // xi_{n-1}
     double K_prev;    // K_{n-1/2}
+    double xi_next;   // xi_n of the next step (from the two above), and its leapfrog factors
+    double A_next;    // 1 - xi_n dt / 2
+    double B_next;    // 1 / (1 + xi_n dt / 2)
     double xi_int;    // sum_k xi_k dt
     double U, W, K_minus, K_plus, xi, px, py, pz;
     long long step;   // completed steps of this replica

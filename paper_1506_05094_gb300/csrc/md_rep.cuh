@@ -240,10 +240,10 @@ __global__ void __launch_bounds__(1024) k_rep(const StepArgs<R> a, const Rebuild
         const int n = S.n, off = S.off;
         const bool rebuild = a.need_in[r] != 0;
         if (threadIdx.x == 0) {
-            const double xi = step_xi(a, S, r);
-            s_xi = xi;
-            s_A = (R)(1.0 - 0.5 * xi * a.dt);
-            s_B = (R)(1.0 / (1.0 + 0.5 * xi * a.dt));
+            const Thermo *T = a.th + r;
+            s_xi = T->xi_next;
+            s_A = (R)T->A_next;
+            s_B = (R)T->B_next;
             s_ovf = 0;
         }
         for (int k = threadIdx.x; k < n; k += blockDim.x) s_pos[k] = a.pos_in[off + k];

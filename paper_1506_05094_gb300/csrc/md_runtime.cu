@@ -700,6 +700,21 @@ void unpack_v4(const md_sim *s, const std::vector<unsigned char> &src, size_t k,
     }
 }
 
+// Host copy of the device's next_factors (md_step.cuh): the Nose-Hoover friction of the next step
+// and its leapfrog factors from the carry; the same IEEE operations in the same order (this file
+// is compiled without FMA contraction), so a loaded state steps exactly like a stepped one.
+void host_next_factors(const md_sim *s, Thermo &T, double K0) {
+    double xi = 0.0;
+    if (s->integrator == MD_NVT_NOSE_HOOVER) {
+        const double inv_tau2 = 1.0 / (s->tau * s->tau);
+        xi = T.xi_prev + (s->dt * (T.K_prev / K0 - 1.0)) * inv_tau2;
+    }
+    const double h = (0.5 * xi) * s->dt;
+    T.xi_next = xi;
+    T.A_next = 1.0 - h;
+    T.B_next = 1.0 / (1.0 + h);
+}
+
 // Interaction range of type pair p: the LJ cutoff, or the Coulomb cutoff if larger.
 double pair_range(const md_sim *s, int p) {
     return s->coul ? std::max(s->params[p].rc, s->rcc) : s->params[p].rc;
@@ -977,6 +992,13 @@ int md_set_integrator(md_sim *s, int kind, double dt, double T, double tau) {
     if (cudaMemcpy(s->b.sys, s->sys.data(), s->sys.size() * sizeof(SysDesc),
                    cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(s, MD_ECUDA);
+    // the next step's friction and factors follow the new integrator, dt, T0 and tau
+    std::vector<Thermo> th(s->R);
+    if (cudaMemcpy(th.data(), s->b.th, sizeof(Thermo) * s->R, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(s, MD_ECUDA);
+    for (int r = 0; r < s->R; ++r) host_next_factors(s, th[r], s->sys[r].K0);
+    if (cudaMemcpy(s->b.th, th.data(), sizeof(Thermo) * s->R, cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(s, MD_ECUDA);
     destroy_graphs(s);
     return MD_OK;
 }
@@ -1053,6 +1075,7 @@ int md_set_state(md_sim *s, int r, const double *pos, const int *type, const dou
     Thermo th;
     std::memset(&th, 0, sizeof(th));
     th.K_prev = K;
+    host_next_factors(s, th, s->sys[r].K0);
     const int one = 1, zero = 0;
     bool ok = true;
     ok = ok && cudaMemcpy((char *)b.pos[cur] + o * R4, mirror.data(), n * R4, cudaMemcpyHostToDevice) == cudaSuccess;

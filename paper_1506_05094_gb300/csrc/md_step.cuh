@@ -326,6 +326,23 @@ __device__ __forceinline__ void tile_partial(const R vals[MD_NRED], double (*s_t
     }
 }
 
+// Nose-Hoover friction of the next step from the carry (Sec. 2), and its leapfrog factors:
+// xi_n = xi_{n-1} + dt (K_{n-1/2} / K0 - 1) / tau^2 (0 for NVE), A = 1 - xi_n dt / 2,
+// B = 1 / (1 + xi_n dt / 2).  Computed once per replica when a step closes (and by the host when
+// a state is loaded), so a tile only reads them; every operation is rounded on its own, so the
+// host's copy of the formula gives the same bits.
+__device__ __forceinline__ void next_factors(Thermo *T, int integrator, double dt, double K0,
+                                             double inv_tau2) {
+    double xi = 0.0;
+    if (integrator == 1)
+        xi = __dadd_rn(T->xi_prev,
+                       __dmul_rn(__dmul_rn(dt, __dsub_rn(__ddiv_rn(T->K_prev, K0), 1.0)), inv_tau2));
+    const double h = __dmul_rn(__dmul_rn(0.5, xi), dt);
+    T->xi_next = xi;
+    T->A_next = __dsub_rn(1.0, h);
+    T->B_next = __ddiv_rn(1.0, __dadd_rn(1.0, h));
+}
+
 // Replica sums over its tile partials (fixed order for a fixed blockDim), thermostat carry,
 // per-step log row and the rebuild flag of the next step.  Call with the whole block.
 // Threads below nthr take tiles tt = thread, thread + nthr, ...; the others add exact zeros, so a
@@ -359,6 +376,7 @@ __device__ __forceinline__ void replica_finish(const StepArgs<R> &a, int r, cons
         T->xi_int += xi * a.dt;
         T->xi_prev = xi;
         T->K_prev = K;
+        next_factors(T, a.integrator, a.dt, S.K0, a.inv_tau2);
         const long long n = T->step;
         T->step = n + 1;
         if (a.log != nullptr && a.log_cap > 0) {
@@ -377,13 +395,6 @@ __device__ __forceinline__ void replica_finish(const StepArgs<R> &a, int r, cons
     }
 }
 
-// Nose-Hoover friction of this step from the previous step's carry (one thread).
-template <typename R>
-__device__ __forceinline__ double step_xi(const StepArgs<R> &a, const SysDesc &S, int r) {
-    if (a.integrator != 1 || a.force_only) return 0.0;
-    const Thermo *T = a.th + r;
-    return T->xi_prev + a.dt * (T->K_prev / S.K0 - 1.0) * a.inv_tau2;
-}
 
 template <typename R>
 __device__ __forceinline__ void load_tables(const StepArgs<R> &a, typename Coef4<R>::t *s_c0,
@@ -454,10 +465,10 @@ __global__ void __launch_bounds__(1024) k_step(const StepArgs<R> a) {
     if (threadIdx.x == 0) {
         // one uniform decision per block: a halt or an unrecovered list overflow stops the step
         s_skip = *(volatile int *)&a.ctrl->halt | *(volatile int *)&a.ctrl->overflow;
-        const double xi = step_xi(a, S, r);
-        s_xi = xi;
-        s_A = (R)(1.0 - 0.5 * xi * a.dt);
-        s_B = (R)(1.0 / (1.0 + 0.5 * xi * a.dt));
+        const Thermo *T = a.th + r;   // this step's friction and factors, set when the last closed
+        s_xi = a.force_only ? 0.0 : T->xi_next;
+        s_A = a.force_only ? R(1) : (R)T->A_next;
+        s_B = a.force_only ? R(1) : (R)T->B_next;
     }
     __syncthreads();
     if (s_skip) return;
