@@ -340,7 +340,10 @@ def time_single_system(name, stream_obj, steps, warmup, peaks=None, p_fp32=None)
     position when peaks are given."""
     wl = synth.workload(name)
     sim = make_sim(wl, stream_obj.cuda_stream)
-    sim.autotune(os.path.join(ROOT, "paper_1506_05094_gb300", "tune_cache.txt"), 50)
+    # a large system rebuilds its list every ~10 steps at a cost of several steps: trials need
+    # enough steps that the number of rebuilds they contain does not decide the comparison
+    trial_steps = 200 if wl.n_total >= 100000 else 50
+    sim.autotune(os.path.join(ROOT, "paper_1506_05094_gb300", "tune_cache.txt"), trial_steps)
     n = wl.n_total
     sim.set_graph_block(1)
     sim.step(SETTLE_STEPS // 4 + max(warmup, 3))
@@ -485,7 +488,7 @@ def main():
     ap.add_argument("--workload", default="ka_ensemble512",
                     choices=sorted(WORKLOAD_NAMES),
                     help="timed workload (default: the batched ensemble)")
-    ap.add_argument("--path", default=None, choices=["grid", "replica", "staged"],
+    ap.add_argument("--path", default=None, choices=["grid", "replica", "staged", "lean"],
                     help="force a kernel path (default: the autotuner's choice)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -528,7 +531,7 @@ def main():
                               tune_skin=True)
     if args.path:
         sim.set_path(args.path)
-    path = {1: "grid", 2: "replica", 3: "staged"}[sim.stats()["path"]]
+    path = {1: "grid", 2: "replica", 3: "staged", 4: "lean"}[sim.stats()["path"]]
     gb = pick_block(args.steps)
     prepare_graphs(sim, gb)          # graphs of both step parities (setup, untimed)
     sim.step(SETTLE_STEPS)           # settle the rebuild schedule (setup, untimed)

@@ -202,10 +202,13 @@ int md_set_list_capacity(md_sim *sim, int n_max);
  * kernels behind a CUDA-graph IF node), 2 = replica-resident kernel (persistent CTAs that each
  * run a whole step of one replica at a time in shared memory, rebuild included), 3 = grid kernels
  * with each tile's replica positions staged in shared memory for the neighbour gathers.  2 and 3
- * are mixed precision only and need replicas that fit in shared memory.  0 = automatic (1; the
- * autotuner times the others).  All paths give the same results bit for bit.  MD_EINVAL if the
- * requested path does not apply. */
-enum { MD_PATH_AUTO = 0, MD_PATH_GRID = 1, MD_PATH_REPLICA = 2, MD_PATH_STAGED = 3 };
+ * are mixed precision only and need replicas that fit in shared memory.  4 = the grid kernels
+ * with the step kernel limited to 48 registers a thread (more resident warps to hide the
+ * neighbour gathers' latency, at the price of a few register spills; faster for large single
+ * systems, slower for small mixed ones).  0 = automatic (1; the autotuner times the others).
+ * All paths give the same results bit for bit.  MD_EINVAL if the requested path does not apply. */
+enum { MD_PATH_AUTO = 0, MD_PATH_GRID = 1, MD_PATH_REPLICA = 2, MD_PATH_STAGED = 3,
+       MD_PATH_LEAN = 4 };
 int md_set_path(md_sim *sim, int path);
 
 /* Steps captured per CUDA graph replay (>= 1; graphs are kept per starting step parity, so an odd

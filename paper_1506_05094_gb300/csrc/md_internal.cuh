@@ -157,6 +157,7 @@ template <typename R> struct StepArgs {
     int coulomb;              // 1: shifted-force Coulomb term between charged types
     int nolist;               // 1: no neighbour list, every pair of the replica is evaluated
     int launch_prio;          // host side: CUDA launch priority of this launch (0 = default)
+    int lean;                 // host side: launch the register-capped step kernel (path 4)
 };
 
 template <typename R> struct RebuildArgs {

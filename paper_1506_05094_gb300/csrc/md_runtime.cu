@@ -467,6 +467,7 @@ cudaError_t do_step(md_sim *s, int parity, cudaStream_t st, int force_only,
         a.has_next = has_next;
         a.need_filter = filter;
         a.launch_prio = filter == 0 ? s->prio_lo : (filter == 1 ? s->prio_hi : 0);
+        a.lean = s->path == 4 ? 1 : 0;
         return launch_step<double>(a, s->tp, s->block, s->ntiles, st);
     }
     StepArgs<float> a = step_args<float>(s, parity, force_only);
@@ -474,6 +475,7 @@ cudaError_t do_step(md_sim *s, int parity, cudaStream_t st, int force_only,
     a.has_next = has_next;
     a.need_filter = filter;
     a.launch_prio = filter == 0 ? s->prio_lo : (filter == 1 ? s->prio_hi : 0);
+    a.lean = s->path == 4 ? 1 : 0;
     if (s->path == 3 && s->staged_ok && s->list_method != 2)
         return launch_step_staged(a, s->tp, s->block, s->ntiles, s->staged_smem, st);
     return launch_step<float>(a, s->tp, s->block, s->ntiles, st);
@@ -1447,7 +1449,7 @@ int md_set_list_capacity(md_sim *s, int n_max) {
 }
 
 int md_set_path(md_sim *s, int path) {
-    if (!s || path < 0 || path > 3) return MD_EINVAL;
+    if (!s || path < 0 || path > 4) return MD_EINVAL;
     if (s->sticky) return s->sticky;
     if (path == 2 && !s->rep_ok) return MD_EINVAL;
     if (path == 3 && !s->staged_ok) return MD_EINVAL;
@@ -1492,7 +1494,7 @@ int md_get_stats(md_sim *s, md_stats *out) {
     out->block = s->block;
     out->reach = s->reach;
     out->build_lanes = s->tpb;
-    out->path = use_rep(s) ? 2 : ((s->path == 3 && s->staged_ok) ? 3 : 1);
+    out->path = use_rep(s) ? 2 : ((s->path == 3 && s->staged_ok) ? 3 : (s->path == 4 ? 4 : 1));
     const int cell_kernels = s->sort_small ? 3 : 7;   // plan, sort (1 or 5 kernels), build
     out->rebuild_kernels = s->list_method == 2   ? 0
                            : s->list_method == 0 ? cell_kernels
@@ -1888,7 +1890,8 @@ extern "C" int md_autotune(md_sim *s, const char *cache_path, int steps, int fla
         if ((e = md_set_rebuild_batch(s, (lanes / 100) % 100))) return e;
         if ((e = md_set_resort_interval(s, cresort))) return e;
         const int path = lanes % 10;
-        return md_set_path(s, (path == 2 && s->rep_ok) || (path == 3 && s->staged_ok) ? path : 1);
+        return md_set_path(s, (path == 2 && s->rep_ok) || (path == 3 && s->staged_ok) || path == 4
+                                  ? path : 1);
     }
     size_t bytes = 0;
     md_checkpoint_size(s, &bytes);
@@ -1948,6 +1951,13 @@ extern "C" int md_autotune(md_sim *s, const char *cache_path, int steps, int fla
         best = std::min(tg, tr);
     }
     if (best >= 1e30 && (rc = trial(best_tp, best_block, best_reach, best_lanes, &best))) return rc;
+    // the register-capped step kernel (path 4) against the chosen one
+    if (s->path == 1) {
+        double tl = 0.0;
+        s->path = 4;
+        if ((rc = trial(best_tp, best_block, best_reach, best_lanes, &tl))) return rc;
+        if (tl < best) best = tl; else s->path = 1;
+    }
     // phase 0b: list method (Appendix phase I: "none" only below 5000 particles, "n2" below 50000)
     {
         int best_m = s->list_method;
@@ -2000,6 +2010,13 @@ extern "C" int md_autotune(md_sim *s, const char *cache_path, int steps, int fla
             if (t > 1.05 * best || ++worse >= 3) break;
         }
         if (best_b >= 1.10 * best) break;
+    }
+    // the register cap again at the best shape (its benefit depends on the block and t_p)
+    if (s->path == 1 || s->path == 4) {
+        const int other = s->path == 1 ? 4 : 1, mine = s->path;
+        s->path = other;
+        if ((rc = trial(best_tp, best_block, best_reach, best_lanes, &t))) return rc;
+        if (t < best) best = t; else s->path = mine;
     }
     // phase III: lanes per particle of the list build (single minimum: walk down, then up);
     // the replica-resident kernel is built for 8 and 32 lanes

@@ -260,8 +260,8 @@ class Sim:
         _ck(lib().md_set_list_method(self._h, int(code)), "md_set_list_method")
 
     def set_path(self, path):
-        """'auto' / 'grid' / 'replica' / 'staged' (or 0 / 1 / 2 / 3)."""
-        code = {"auto": 0, "grid": 1, "replica": 2, "staged": 3}.get(path, path)
+        """'auto' / 'grid' / 'replica' / 'staged' / 'lean' (or 0 / 1 / 2 / 3 / 4)."""
+        code = {"auto": 0, "grid": 1, "replica": 2, "staged": 3, "lean": 4}.get(path, path)
         _ck(lib().md_set_path(self._h, int(code)), "md_set_path")
 
     def set_graph_block(self, steps: int):

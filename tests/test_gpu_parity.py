@@ -439,12 +439,12 @@ def _traj(sts, path, steps, tuning=(1, 128, 2, 8), graph_block=20):
     return out, en, st
 
 
-@pytest.mark.parametrize("path,code", [("replica", 2), ("staged", 3)])
+@pytest.mark.parametrize("path,code", [("replica", 2), ("staged", 3), ("lean", 4)])
 @pytest.mark.parametrize("tuning", [(1, 128, 2, 8), (4, 256, 2, 32), (2, 64, 3, 8)])
 def test_kernel_paths_bit_identical_to_grid(path, code, tuning):
-    """Same slot order, list order and reduction tree: the replica-resident kernel and the grid
-    kernel with staged positions agree with the grid kernel bit for bit (NVT, 300 steps, with
-    rebuilds)."""
+    """Same slot order, list order and reduction tree: the replica-resident kernel, the grid
+    kernel with staged positions and the register-capped grid kernel agree with the grid kernel
+    bit for bit (NVT, 300 steps, with rebuilds)."""
     sts = _ensemble([512, 1000, 700, 2048, 777, 1500])
     a, ea, sa = _traj(sts, path, 300, tuning)
     b, eb, sb = _traj(sts, "grid", 300, tuning)
