@@ -179,9 +179,9 @@ def step_kernel_bytes(n_total: int, entries: int, precision: str) -> float:
     """Algorithmic bytes of one fused step-kernel launch.
 
     Per particle: neighbour indices 4 n_i; own position (16) + count (4); each neighbour
-    position counted once (16, reuse served on chip); velocity read+write (32); FP64 master
-    position read+write (48); new position mirror write (16); build position read (16).
-    FP64 mode doubles the Real4 quantities.
+    position counted once (16, reuse served on chip); velocity read+write (32); master
+    position read+write (48: 64-bit fixed point in mixed precision, FP64 in FP64 mode); new
+    position mirror write (16); build position read (16). FP64 mode doubles the 16-byte vectors.
     """
     r4 = 32 if precision == "fp64" else 16
     per = r4 + 4 + r4 + 2 * r4 + 48 + r4 + r4
