@@ -188,8 +188,11 @@ int md_get_neighbors(md_sim *sim, int replica, int max_per_particle, int *counts
 /* Kernel shape: tp in {1,2,4,8,16,32} threads per particle in the force kernel (Sec. 3 t_p),
  * block threads per CTA (multiple of 32, tp <= block <= 1024), reach in {1,2,3}: cell edge
  * >= (rc_max + skin)/reach with a (2 reach + 1)^3 stencil (Sec. 7 uses reach 2), build_lanes in
- * {1,2,4,8,16,32} lanes per particle in the list build (Sec. 7 uses one thread per particle;
- * the list order, hence every result bit, does not depend on it).  0 keeps the current value. */
+ * {1,2,4,8,16,32} lanes per particle in the list build (Sec. 7 uses one thread per particle), or
+ * MD_BUILD_CELL: one warp per cell builds the lists of all the cell's particles, loading each
+ * stencil candidate once for the whole cell (grid kernel paths only).  The list order, hence
+ * every result bit, does not depend on build_lanes.  0 keeps the current value. */
+enum { MD_BUILD_CELL = 64 };
 int md_set_tuning(md_sim *sim, int tp, int block, int reach, int build_lanes);
 int md_get_tuning(md_sim *sim, int *tp, int *block, int *reach, int *build_lanes);
 

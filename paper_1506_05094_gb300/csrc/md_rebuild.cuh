@@ -428,6 +428,151 @@ template <typename R, int TPB> __global__ void __launch_bounds__(MD_BUILD_BLOCK,
 }
 
 // ------------------------------------------------------------------------------------------------
+// List build with one warp per cell (build_lanes = MD_BUILD_CELL).  Every particle of a cell
+// searches the same stencil of cells (Fig. 4), so the warp walks the cell's stencil ranges once,
+// 32 candidates at a time (one per lane, consecutive sorted slots), and tests each batch against
+// up to MD_CELL_CHUNK particles of the cell read from shared memory.  Accepted candidates are
+// compacted per particle by ballot in candidate order.  The ranges are build_one's in the same
+// order without its per-particle clipping; the clipping drops only cells that hold no neighbour
+// of the particle and keeps the order of the rest, so every list is the same as build_one's, bit
+// for bit.
+// ------------------------------------------------------------------------------------------------
+#define MD_CELL_CHUNK 8
+
+template <typename R>
+__global__ void __launch_bounds__(MD_BUILD_BLOCK, 8) k_build_cell(const RebuildArgs<R> a) {
+    typedef typename V4T<R>::t V4;
+    constexpr int NW = MD_BUILD_BLOCK / 32;
+    if (cells_off(a)) return;
+    __shared__ R s_thr[MD_MAX_PAIRS];
+    __shared__ int s_lo[NW][MD_MAX_RANGES];        // first slot of each nonempty range
+    __shared__ int s_pre[NW][MD_MAX_RANGES + 1];   // its first candidate in the cell's order
+    __shared__ V4 s_ki[NW][MD_CELL_CHUNK];
+    const int npair = a.ntypes * a.ntypes;
+    for (int p = threadIdx.x; p < npair; p += blockDim.x)
+        s_thr[p] = sizeof(R) == 4 ? (R)a.tab[p].thr2 : (R)a.tab[p].thr2d;
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    const int tot = a.plan->tot_c, nf = a.plan->nflag;
+    const V4 *Kp = a.key_is_pos ? a.tpos : a.tkey;
+    int *lo_w = s_lo[warp], *pre_w = s_pre[warp];
+    V4 *ki_w = s_ki[warp];
+    for (int t = blockIdx.x * NW + warp; t < tot; t += gridDim.x * NW) {
+        const int k = find_seg(a.plan_pc, nf, t);
+        const SysDesc &S = a.sys[a.plan_rep[k]];
+        const int cl = t - a.plan_pc[k];
+        const int p0 = a.cell_start[S.cell_off + cl], p1 = a.cell_start[S.cell_off + cl + 1];
+        if (p0 == p1) continue;
+        const int nc = S.nc, span = S.span, reach = S.reach;
+        const int cx = cl % nc, cy = (cl / nc) % nc, cz = cl / (nc * nc);
+        const bool full = (span == nc);
+        // the stencil's ranges: row q/2 in (z, y) order, part q%2 of its x extent
+        const int nr = span * span * 2;
+        int total = 0, nq = 0;
+        for (int q0 = 0; q0 < nr; q0 += 32) {
+            const int q = q0 + lane;
+            int lo = 0, len = 0;
+            if (q < nr) {
+                const int rowi = q >> 1, part = q & 1;
+                const int oz = rowi / span, oy = rowi % span;
+                int x0 = 0, x1 = nc - 1;
+                bool has = (part == 0);
+                if (!full) {
+                    const int a0 = cx - reach, a1 = cx + reach;
+                    if (a0 < 0) { has = true; x0 = part ? 0 : a0 + nc; x1 = part ? a1 : nc - 1; }
+                    else if (a1 >= nc) { has = true; x0 = part ? 0 : a0; x1 = part ? a1 - nc : nc - 1; }
+                    else { x0 = a0; x1 = a1; }
+                }
+                if (has) {
+                    const int zz = full ? oz : (cz - reach + oz + nc) % nc;
+                    const int yy = full ? oy : (cy - reach + oy + nc) % nc;
+                    const int row = S.cell_off + (zz * nc + yy) * nc;
+                    lo = a.cell_start[row + x0];
+                    len = a.cell_start[row + x1 + 1] - lo;
+                }
+            }
+            // keep the nonempty ranges in order, with the running candidate count
+            const unsigned ne = __ballot_sync(FULL_MASK, len > 0);
+            int incl = len;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(FULL_MASK, incl, o);
+                if (lane >= o) incl += v;
+            }
+            if (len > 0) {
+                const int pos = nq + __popc(ne & below);
+                lo_w[pos] = lo;
+                pre_w[pos] = total + incl - len;
+            }
+            total += __shfl_sync(FULL_MASK, incl, 31);
+            nq += __popc(ne);
+        }
+        if (lane == 0) pre_w[nq] = total;
+        __syncwarp();
+        for (int pb = p0; pb < p1; pb += MD_CELL_CHUNK) {
+            const int np = min(MD_CELL_CHUNK, p1 - pb);
+            if (lane < np) ki_w[lane] = Kp[pb + lane];
+            __syncwarp();
+            int cnt[MD_CELL_CHUNK];
+#pragma unroll
+            for (int p = 0; p < MD_CELL_CHUNK; ++p) cnt[p] = 0;
+            int q = 0;   // this lane's current range
+            for (int f0 = 0; f0 < total; f0 += 32) {
+                const int f = f0 + lane;
+                const bool valid = f < total;
+                int j = -1, tj = 0;
+                V4 kj = ki_w[0];
+                if (valid) {
+                    while (pre_w[q + 1] <= f) ++q;
+                    j = lo_w[q] + (f - pre_w[q]);
+                    kj = Kp[j];
+                    tj = type_of(kj);
+                }
+#pragma unroll
+                for (int p = 0; p < MD_CELL_CHUNK; ++p) {
+                    if (p < np) {
+                        const V4 ki = ki_w[p];
+                        const bool ok = valid && j != pb + p &&
+                                        key_dist2(ki, kj, S) < s_thr[type_of(ki) * a.ntypes + tj];
+                        const unsigned m = __ballot_sync(FULL_MASK, ok);
+                        if (ok) {
+                            const int sl = cnt[p] + __popc(m & below);
+                            if (sl < a.nmax) a.nbl[nbl_offset(pb + p, sl, a.nmax)] = j;
+                        }
+                        cnt[p] += __popc(m);
+                    }
+                }
+            }
+            int mine = 0;
+#pragma unroll
+            for (int p = 0; p < MD_CELL_CHUNK; ++p) {
+                if (p < np) pad_list(a.nbl, pb + p, cnt[p], a.nmax, a.pad, lane, 32);
+                if (lane == p) mine = cnt[p];
+            }
+            if (lane < np) {
+                const int i = pb + lane;
+                if (mine > a.nmax) {   // Sec. 4: out of space -> flag for the host
+                    atomicMax(&a.ctrl->max_count, mine);
+                    atomicExch(&a.ctrl->overflow, 1);
+                    mine = a.nmax;
+                }
+                a.nnb[i] = mine;
+                a.pos[i] = a.tpos[i];
+                a.pos_build[i] = Kp[i];
+                a.xm[i] = a.txm[i];
+                a.ym[i] = a.tym[i];
+                a.zm[i] = a.tzm[i];
+                a.vel[i] = a.tvel[i];
+                a.img[i] = a.timg[i];
+                a.id[i] = a.tid[i];
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
 // O(N^2) list build (Sec. 6, Fig. 3): TPB lanes per rebuilt particle scan every particle of its
 // replica in slot order (no cell sort), test the same bit-defined FP32 rule as the cell build and
 // compact the accepted slots by ballot in slot order.  The build positions are the current ones.

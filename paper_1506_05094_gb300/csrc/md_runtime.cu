@@ -161,6 +161,7 @@ void destroy_graphs(md_sim *s) {
 bool is_pow2_tp(int tp) {
     return tp == 1 || tp == 2 || tp == 4 || tp == 8 || tp == 16 || tp == 32;
 }
+bool valid_lanes(int lanes) { return is_pow2_tp(lanes) || lanes == MD_BUILD_CELL; }
 
 // Cells per box edge for a stencil reach: edge >= (rc_max + skin) / reach with a 1e-4 margin
 // so that FP32 rounding of the cell coordinate never breaks the stencil guarantee.
@@ -1316,7 +1317,7 @@ int md_set_tuning(md_sim *s, int tp, int block, int reach, int build_lanes) {
     const int ntp = tp ? tp : s->tp, nb = block ? block : s->block, nr = reach ? reach : s->reach;
     const int nl = build_lanes ? build_lanes : s->tpb;
     if (!is_pow2_tp(ntp) || nb < 32 || nb > 1024 || (nb % 32) != 0 || nb < ntp || nr < 1 ||
-        nr > 3 || !is_pow2_tp(nl))
+        nr > 3 || !valid_lanes(nl))
         return MD_EINVAL;
     if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(s, MD_ECUDA);
     const bool cells_change = nr != s->reach;
@@ -1881,7 +1882,7 @@ extern "C" int md_autotune(md_sim *s, const char *cache_path, int steps, int fla
     if (cache_lookup(cache_path, key, &tp, &block, &reach, &lanes, &cskin, &cresort) &&
         is_pow2_tp(tp) && cresort >= 0 &&
         block >= tp && block <= 1024 && block % 32 == 0 && reach >= 1 && reach <= 3 &&
-        is_pow2_tp(lanes / 10000) && lanes % 10 <= 3 && (lanes / 10) % 10 <= 2 &&
+        valid_lanes(lanes / 10000) && lanes % 10 <= 4 && (lanes / 10) % 10 <= 2 &&
         (lanes / 100) % 100 >= 1) {
         int e = 0;
         if ((flags & MD_TUNE_SKIN) && cskin > 0.0 && (e = md_set_skin(s, cskin))) return e;
@@ -2029,6 +2030,11 @@ extern "C" int md_autotune(md_sim *s, const char *cache_path, int steps, int fla
             if ((rc = trial(best_tp, best_block, best_reach, la, &t))) return rc;
             if (t < best) { best = t; best_lanes = la; } else break;
         }
+    }
+    // ... and the build with one warp per cell (grid kernel paths)
+    if (s->path != 2) {
+        if ((rc = trial(best_tp, best_block, best_reach, MD_BUILD_CELL, &t))) return rc;
+        if (t < best) { best = t; best_lanes = MD_BUILD_CELL; }
     }
     if ((rc = md_set_tuning(s, best_tp, best_block, best_reach, best_lanes))) return rc;
     if ((rc = md_set_graph_block(s, gb_saved))) return rc;

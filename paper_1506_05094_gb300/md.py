@@ -20,6 +20,7 @@ MD_OK, MD_EINVAL, MD_ENOMEM, MD_ECUDA, MD_EUNSTABLE, MD_ETIMEOUT, MD_ESTATE = ra
 MD_SHIFTED_POTENTIAL, MD_SHIFTED_FORCE = 0, 1
 MD_MIXED, MD_FP64 = 0, 1
 MD_NVE_LEAPFROG, MD_NVT_NOSE_HOOVER = 0, 1
+MD_BUILD_CELL = 64   # build_lanes value: one warp per cell builds the lists of its particles
 LOG_COLS = ("step", "U", "W", "K_minus", "K_plus", "xi", "xi_int", "H", "px", "py", "pz")
 
 # every function declared in include/md.h

@@ -17,6 +17,7 @@ import pytest
 import oracle
 import synth
 from gpu_util import f32, ka, lj, make_sim, rel_rms, dev_pos, dev_q
+from paper_1506_05094_gb300 import md
 
 pytestmark = pytest.mark.gpu
 
@@ -134,13 +135,14 @@ def test_neighbor_sets_bit_exact(n, reach):
         np.testing.assert_array_equal(got, ref[i])
 
 
-@pytest.mark.parametrize("reach", [1, 2])
+@pytest.mark.parametrize("reach", [1, 2, 3])
 def test_list_order_and_forces_independent_of_build_lanes(reach):
     """The list build compacts accepted candidates in candidate order, so the list (order
-    included) and therefore the forces are bitwise the same for any lanes-per-particle."""
+    included) and therefore the forces are bitwise the same for any lanes-per-particle and for
+    the build with one warp per cell (reach 1: ~26 particles per cell, several chunks)."""
     st = ka(1500, seed=77)
     ref = None
-    for lanes in (1, 4, 8, 32):
+    for lanes in (1, 4, 8, 32, md.MD_BUILD_CELL):
         with make_sim(KA, [st], tuning=(2, 128, reach, lanes)) as sim:
             f, u, w = sim.forces(0)
             counts, nb = sim.neighbors(0)
@@ -150,6 +152,29 @@ def test_list_order_and_forces_independent_of_build_lanes(reach):
         np.testing.assert_array_equal(counts, ref[1])
         np.testing.assert_array_equal(nb, ref[2])
         np.testing.assert_array_equal(f, ref[0])
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_cell_build_trajectory_bitwise_equal_to_particle_build(precision):
+    """Replicas of several sizes (N = 256 has fewer cells per edge than the stencil and searches
+    the whole box) stepped through their skin-triggered rebuilds: the build with one warp per cell
+    gives the same lists, hence the same trajectory bit for bit, as 8 lanes per particle."""
+    states = [ka(n, seed=300 + n) for n in (256, 1100, 2900)]
+    out = []
+    for lanes in (8, md.MD_BUILD_CELL):
+        with make_sim(KA, states, precision=precision, integrator="nvt", dt=0.0025, T=0.8,
+                      tau=0.2, tuning=(1, 128, 2, lanes), graph_block=50) as sim:
+            sim.step(300)
+            out.append([sim.get_state(r) for r in range(len(states))] +
+                       [sim.energies(r)["U"] for r in range(len(states))] +
+                       [sim.stats()["replica_rebuilds"]])
+    assert out[0][-1] > 3 * len(states)   # rebuilds happened during the steps
+    for a, b in zip(out[0], out[1]):
+        if isinstance(a, tuple):
+            for x, y in zip(a, b):
+                np.testing.assert_array_equal(x, y)
+        else:
+            assert a == b
 
 
 def test_neighbor_sets_fp64_mode_near_threshold_only():
