@@ -402,7 +402,7 @@ template <typename R, int TPB> __global__ void __launch_bounds__(MD_BUILD_BLOCK,
     for (int g = blockIdx.x * (blockDim.x / TPB) + threadIdx.x / TPB; g < tot; g += groups) {
         int r, i;
         pass_particle(a.plan_pp, a.plan_rep, nf, g, a.sys, r, i);
-        const SysDesc &S = a.sys[r];
+        const SysDesc S = a.sys[r];   // a copy: the list stores cannot alias it
         GlobalKey<R> K{Kp};
         GlobalStart CS{a.cell_start, S.cell_off};
         int cnt = build_one<R, TPB, true>(S, K, CS, i, i, 0, a.nbl, a.nmax, s_thr, a.ntypes,
@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(MD_BUILD_BLOCK, 8) k_build_cell(const RebuildA
     V4 *ki_w = s_ki[warp];
     for (int t = blockIdx.x * NW + warp; t < tot; t += gridDim.x * NW) {
         const int k = find_seg(a.plan_pc, nf, t);
-        const SysDesc &S = a.sys[a.plan_rep[k]];
+        const SysDesc S = a.sys[a.plan_rep[k]];   // a copy: the list stores cannot alias it
         const int cl = t - a.plan_pc[k];
         const int p0 = a.cell_start[S.cell_off + cl], p1 = a.cell_start[S.cell_off + cl + 1];
         if (p0 == p1) continue;
@@ -594,7 +594,7 @@ __global__ void __launch_bounds__(MD_BUILD_BLOCK) k_build_n2(const RebuildArgs<R
     for (int g = blockIdx.x * (blockDim.x / TPB) + threadIdx.x / TPB; g < tot; g += groups) {
         int r, i;
         pass_particle(a.plan_pp, a.plan_rep, nf, g, a.sys, r, i);
-        const SysDesc &S = a.sys[r];
+        const SysDesc S = a.sys[r];   // a copy: the list stores cannot alias it
         const V4 ki = a.key[i];
         const int ti = type_of(ki);
         int cnt = 0;
