@@ -286,11 +286,11 @@ def l2_flush_buffer():
 
 def time_steps_flushed(sim, stream_obj, steps: int, per_step: list | None = None):
     """Sum of per-step durations (CUDA events on the sim's stream), the L2 flushed by a 256 MB
-    write before every step; each step is one replay of a one-step CUDA graph."""
+    write before every step; each step is one replay of a one-step CUDA graph (the caller
+    captures the graphs of both step parities first, with prepare_graphs(sim, 1))."""
     import torch
 
     flush = l2_flush_buffer()
-    prepare_graphs(sim, 1)           # capture the graphs of both step parities (untimed)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     tot = 0.0
@@ -351,7 +351,10 @@ def time_single_system(name, stream_obj, steps, warmup, peaks=None, p_fp32=None)
     ws_bytes = 4.0 * st0["neighbor_entries"] + 100.0 * n
     out = {"workload": name, "n": n, "working_set_mb": ws_bytes / 1e6}
     if ws_bytes < L2_BYTES:
+        prepare_graphs(sim, 1)       # graphs of both step parities (untimed)
+        b0 = sim.stats()["graph_builds"]
         tot = time_steps_flushed(sim, stream_obj, steps)
+        assert sim.stats()["graph_builds"] == b0
         out.update(ms_per_step_flushed=tot / steps, value_flushed=n * steps / (tot / 1e3))
     # back-to-back graph replay (L2 warm when the working set fits; stated above)
     prepare_graphs(sim, GRAPH_BLOCK)

@@ -210,34 +210,32 @@ template <typename R> __global__ void k_scatter(const RebuildArgs<R> a) {
 }
 
 // Atomic slot order inside a cell is arbitrary (as with atomicInc in Sec. 6); restore a
-// deterministic order: by user id.
+// deterministic order: by user id.  Each particle counts the members of its cell (listed in
+// atomic order by k_scatter) that have a smaller id: that count is its place in the cell's
+// id-sorted order.  The counts reuse the atomic-rank array, which k_scatter has consumed.
 template <typename R> __global__ void k_cellsort(const RebuildArgs<R> a) {
     if (cells_off(a)) return;
-    const int tot = a.plan->tot_c, nf = a.plan->nflag;
+    const int tot = a.plan->tot_p, nf = a.plan->nflag;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
-        const int k = find_seg(a.plan_pc, nf, t);
-        const int c = a.sys[a.plan_rep[k]].cell_off + (t - a.plan_pc[k]);
+        int r, i;
+        pass_particle(a.plan_pp, a.plan_rep, nf, t, a.sys, r, i);
+        const int c = a.cell_of[i];
         const int s = a.cell_start[c], e = a.cell_start[c + 1];
-        for (int q = s + 1; q < e; ++q) {
-            const int v = a.perm[q];
-            const int key = a.id[v];
-            int m = q - 1;
-            while (m >= s && a.id[a.perm[m]] > key) {
-                a.perm[m + 1] = a.perm[m];
-                --m;
-            }
-            a.perm[m + 1] = v;
-        }
+        const int key = a.id[i];
+        int below = 0;
+        for (int q = s; q < e; ++q) below += a.id[a.perm[q]] < key ? 1 : 0;
+        a.rank[i] = below;
     }
 }
 
+// Every rebuilt particle's data to its sorted slot (cell start + place in the cell) in scratch.
 template <typename R> __global__ void k_gather(const RebuildArgs<R> a) {
     if (cells_off(a)) return;
     const int tot = a.plan->tot_p, nf = a.plan->nflag;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
-        int r, s;
-        pass_particle(a.plan_pp, a.plan_rep, nf, t, a.sys, r, s);
-        const int o = a.perm[s];
+        int r, o;
+        pass_particle(a.plan_pp, a.plan_rep, nf, t, a.sys, r, o);
+        const int s = a.cell_start[a.cell_of[o]] + a.rank[o];
         a.tpos[s] = a.pos[o];
         if (!a.key_is_pos) a.tkey[s] = a.key[o];
         a.txm[s] = a.xm[o];

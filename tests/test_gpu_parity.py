@@ -135,6 +135,27 @@ def test_neighbor_sets_bit_exact(n, reach):
         np.testing.assert_array_equal(got, ref[i])
 
 
+def test_grid_sort_lists_match_oracle_and_repeat_bitwise():
+    """N = 20000 is past the one-CTA sort (16384 particles), so the cells are sorted by the grid
+    kernels: atomic binning, then each particle's place in its cell by id.  The pair sets equal
+    the oracle's, and two independent runs (8 lanes per particle, then a warp per cell) give the
+    same lists in the same order (the atomic order differs between runs; the id order does not)
+    and the same forces bit for bit."""
+    st = ka(20000, seed=2020)
+    runs = []
+    for lanes in (8, md.MD_BUILD_CELL):
+        with make_sim(KA, [st], tuning=(1, 128, 2, lanes)) as sim:
+            f, u, w = sim.forces(0)
+            counts, nb = sim.neighbors(0)
+        runs.append((f, counts, nb))
+    ref, rc = oracle.neighbors_fixed(dev_q(st.pos, st.L), st.types, st.L, KA, 0.3, maxn=256)
+    np.testing.assert_array_equal(runs[0][1], rc)
+    for i in range(0, st.n, 7):
+        np.testing.assert_array_equal(np.sort(runs[0][2][i, :rc[i]]), ref[i])
+    for x, y in zip(runs[0], runs[1]):
+        np.testing.assert_array_equal(x, y)
+
+
 @pytest.mark.parametrize("reach", [1, 2, 3])
 def test_list_order_and_forces_independent_of_build_lanes(reach):
     """The list build compacts accepted candidates in candidate order, so the list (order
