@@ -139,10 +139,13 @@ int md_set_integrator(md_sim *sim, int kind, double dt, double T, double tau);
  * positions, types and velocities; here the caller passes it as arrays instead of a file):
  * pos (n,3) in any periodic image (wrapped into [0,L) here, the wrap added to the image
  * counters), type (n) in [0,n_types), vel (n,3) = v(t - dt/2) (the leapfrog half step of the
- * Sec. 2 integrators), image (n,3) or NULL.  Host arrays, copied in; the caller keeps them.
+ * Sec. 2 integrators), image (n,3) or NULL.  Host arrays, read before the call returns; the
+ * caller keeps them.  The state is packed on the host into a pinned staging area and loaded on
+ * the md_sim's stream behind the steps already queued there, so the call does not wait for
+ * the device (a later call on this md_sim, or md_sync, sees it complete).
  * Resets the replica's thermostat (xi = 0) and step record, and forces a list rebuild.
  * MD_EINVAL for a bad replica index, a NULL array, a type outside [0,n_types) or a non-finite
- * value (nothing is changed); MD_ECUDA (sticky) if a copy fails. */
+ * value (nothing is changed); MD_ECUDA (sticky) if a copy or launch fails. */
 int md_set_state(md_sim *sim, int replica, const double *pos, const int *type, const double *vel,
                  const int *image);
 
@@ -165,8 +168,9 @@ int md_sync(md_sim *sim);
 
 /* Copy replica r out in user order (the configuration that Sec. 2 saves to disk, positions with
  * their periodic images): pos (n,3) wrapped into [0,L), image (n,3), vel (n,3) = v(t - dt/2).
- * Host arrays owned by the caller; any pointer may be NULL.  MD_ESTATE before md_set_state of
- * this replica, MD_EINVAL for a bad replica index. */
+ * Host arrays owned by the caller; any pointer may be NULL.  Waits for the steps queued on the
+ * md_sim's stream.  MD_ESTATE before md_set_state of this replica, MD_EINVAL for a bad replica
+ * index. */
 int md_get_state(md_sim *sim, int replica, double *pos, int *image, double *vel);
 
 /* Thermodynamic record of replica r (see md_energies): the energy, virial, pressure and

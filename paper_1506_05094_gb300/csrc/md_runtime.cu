@@ -100,6 +100,13 @@ struct md_sim {
     long long overflows = 0;
     int device = 0;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    // state transfers (md_set_state / md_get_state) go through one packed staging area: two
+    // pinned host halves (one is packed while the other's copy runs) and one device buffer,
+    // each for stage_cap particles
+    unsigned char *stage_h[2] = {nullptr, nullptr};
+    void *stage_d = nullptr;
+    cudaEvent_t stage_ev[2] = {nullptr, nullptr};
+    int stage_k = 0, stage_cap = 0;
 };
 
 namespace {
@@ -655,53 +662,158 @@ int check_replica(md_sim *s, int r) {
     return MD_OK;
 }
 
+template <typename R> void pack_v4(unsigned char *dst, size_t k, double x, double y, double z,
+                                   double w) {
+    R v[4] = {(R)x, (R)y, (R)z, (R)w};
+    std::memcpy(dst + k * sizeof(v), v, sizeof(v));
+}
 template <typename R> void pack_v4(std::vector<unsigned char> &dst, size_t k, double x, double y,
                                    double z, double w) {
-    R v[4] = {(R)x, (R)y, (R)z, (R)w};
-    std::memcpy(dst.data() + k * sizeof(v), v, sizeof(v));
+    pack_v4<R>(dst.data(), k, x, y, z, w);
 }
 
 // Mixed precision keeps positions in fixed point (the kernels' layout notes give the units):
 // master = round(x / L 2^64) of a coordinate folded into [0, L) (a value that rounds to 2^64,
 // i.e. to L, is 0), mirror = the master rounded to 32 bits.  Every step is an IEEE double
 // operation or an integer one, so both host architectures give the same bits.
+// (Scaling by 2^64 or 2^-64 is exact, and a double of 2^52 or more is already an integer, so the
+// rounding call is needed only below 2^52.)
 uint64_t to_fixed64(double x, double L) {
-    const double q = std::nearbyint(std::ldexp(x / L, 64));
+    double q = (x / L) * 18446744073709551616.0;   // x / L * 2^64
+    if (q < 4503599627370496.0) q = std::nearbyint(q);   // 2^52
     if (!(q < 18446744073709551616.0)) return 0;   // 2^64: the period itself
     return q <= 0.0 ? 0 : (uint64_t)q;
 }
 // back to a coordinate in [0, L)
 double from_fixed64(uint64_t q, double L) {
-    const double x = std::ldexp((double)q, -64) * L;
+    const double x = ((double)q * 5.421010862427522170037264e-20) * L;   // q 2^-64 L
     return x < L ? x : std::nextafter(L, 0.0);
 }
 int32_t mirror32(uint64_t q) { return (int32_t)(uint32_t)((q + 0x80000000ull) >> 32); }
 
 // FP64 mirror: x, y, z and the type's bits in .w
-void pack_pos(std::vector<unsigned char> &dst, size_t k, double x, double y, double z, int type) {
+void pack_pos(unsigned char *dst, size_t k, double x, double y, double z, int type) {
     double v[4] = {x, y, z, 0.0};
     long long t = type;
     std::memcpy(&v[3], &t, sizeof(double));
-    std::memcpy(dst.data() + k * 32, v, 32);
+    std::memcpy(dst + k * 32, v, 32);
+}
+void pack_pos(std::vector<unsigned char> &dst, size_t k, double x, double y, double z, int type) {
+    pack_pos(dst.data(), k, x, y, z, type);
 }
 // fixed-point mirror of a mixed-precision master position
+void pack_mirror(unsigned char *dst, size_t k, uint64_t qx, uint64_t qy, uint64_t qz, int type) {
+    const int32_t v[4] = {mirror32(qx), mirror32(qy), mirror32(qz), type};
+    std::memcpy(dst + k * 16, v, 16);
+}
 void pack_mirror(std::vector<unsigned char> &dst, size_t k, uint64_t qx, uint64_t qy, uint64_t qz,
                  int type) {
-    const int32_t v[4] = {mirror32(qx), mirror32(qy), mirror32(qz), type};
-    std::memcpy(dst.data() + k * 16, v, 16);
+    pack_mirror(dst.data(), k, qx, qy, qz, type);
 }
 
-void unpack_v4(const md_sim *s, const std::vector<unsigned char> &src, size_t k, double *out3) {
+void unpack_v4(const md_sim *s, const unsigned char *src, size_t k, double *out3) {
     if (s->precision == MD_FP64) {
         double v[4];
-        std::memcpy(v, src.data() + k * 32, 32);
+        std::memcpy(v, src + k * 32, 32);
         out3[0] = v[0]; out3[1] = v[1]; out3[2] = v[2];
     } else {
         float v[4];
-        std::memcpy(v, src.data() + k * 16, 16);
+        std::memcpy(v, src + k * 16, 16);
         out3[0] = v[0]; out3[1] = v[1]; out3[2] = v[2];
     }
 }
+void unpack_v4(const md_sim *s, const std::vector<unsigned char> &src, size_t k, double *out3) {
+    unpack_v4(s, src.data(), k, out3);
+}
+
+// ---- packed state transfers
+// One chunk of a replica's state in the staging area, particles k0 .. k0 + n - 1 (user order on
+// the way in, slot order on the way out).  In: mirror records, velocity records, image counters,
+// then the x, y and z masters (8 bytes each: doubles, or 64-bit fixed point).  Out: velocity
+// records, image counters, x, y, z masters, user ids.  Records are R4 bytes (r4w int4 words).
+constexpr int kStageChunk = 1 << 16;
+size_t stage_bytes_per_particle(size_t R4) { return 2 * R4 + 48; }
+
+struct StateXfer {
+    void *stage;
+    int n, k0, o, r4w;
+    int4 *pos, *pos_build, *vel;
+    unsigned long long *x, *y, *z;
+    int4 *img;
+    int *id, *nnb;
+};
+
+__global__ void k_load_state(const StateXfer t) {
+    const int4 *mir = (const int4 *)t.stage;
+    const int4 *vel = mir + (size_t)t.n * t.r4w;
+    const int4 *img = vel + (size_t)t.n * t.r4w;
+    const unsigned long long *x = (const unsigned long long *)(img + t.n);
+    const unsigned long long *y = x + t.n, *z = y + t.n;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < t.n; k += gridDim.x * blockDim.x) {
+        const size_t d = (size_t)t.o + t.k0 + k;
+        for (int w = 0; w < t.r4w; ++w) {
+            const int4 m = mir[(size_t)k * t.r4w + w];
+            t.pos[d * t.r4w + w] = m;
+            t.pos_build[d * t.r4w + w] = m;
+            t.vel[d * t.r4w + w] = vel[(size_t)k * t.r4w + w];
+        }
+        t.x[d] = x[k];
+        t.y[d] = y[k];
+        t.z[d] = z[k];
+        t.img[d] = img[k];
+        t.id[d] = t.k0 + k;
+        t.nnb[d] = 0;
+    }
+}
+
+// the replica's carry and flags after its particles are loaded: thermostat state, a rebuild
+// request for the next step, no displacement since the (pending) build
+__global__ void k_load_replica(const Thermo th, Thermo *th_dst, int *need, int *moved,
+                               unsigned *disp, Ctrl *ctrl) {
+    *th_dst = th;
+    *need = 1;
+    *moved = 0;
+    disp[0] = 0u;
+    disp[1] = 0u;
+    ctrl->need_any = 1;
+}
+
+__global__ void k_save_state(const StateXfer t) {
+    int4 *vel = (int4 *)t.stage;
+    int4 *img = vel + (size_t)t.n * t.r4w;
+    unsigned long long *x = (unsigned long long *)(img + t.n);
+    unsigned long long *y = x + t.n, *z = y + t.n;
+    int *id = (int *)(z + t.n);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < t.n; k += gridDim.x * blockDim.x) {
+        const size_t d = (size_t)t.o + t.k0 + k;
+        for (int w = 0; w < t.r4w; ++w) vel[(size_t)k * t.r4w + w] = t.vel[d * t.r4w + w];
+        img[k] = t.img[d];
+        x[k] = t.x[d];
+        y[k] = t.y[d];
+        z[k] = t.z[d];
+        id[k] = t.id[d];
+    }
+}
+
+StateXfer state_xfer(md_sim *s, int r, int k0, int n) {
+    StateXfer t;
+    t.stage = s->stage_d;
+    t.n = n;
+    t.k0 = k0;
+    t.o = s->off[r];
+    t.r4w = (int)(s->r4 / 16);
+    t.pos = (int4 *)s->b.pos[s->h_step & 1];
+    t.pos_build = (int4 *)s->b.pos_build;
+    t.vel = (int4 *)s->b.vel;
+    t.x = (unsigned long long *)s->b.xd;
+    t.y = (unsigned long long *)s->b.yd;
+    t.z = (unsigned long long *)s->b.zd;
+    t.img = s->b.img;
+    t.id = s->b.id;
+    t.nnb = s->b.nnb;
+    return t;
+}
+int xfer_grid(int n) { return std::max(1, std::min((n + 255) / 256, 1024)); }
 
 // Host copy of the device's next_factors (md_step.cuh): the Nose-Hoover friction of the next step
 // and its leapfrog factors from the carry; the same IEEE operations in the same order (this file
@@ -775,6 +887,11 @@ void md_destroy(md_sim *s) {
     }
     if (s->rep_order) cudaFree(s->rep_order);
     if (s->h_ctrl) cudaFreeHost(s->h_ctrl);
+    for (int h = 0; h < 2; ++h) {
+        if (s->stage_h[h]) cudaFreeHost(s->stage_h[h]);
+        if (s->stage_ev[h]) cudaEventDestroy(s->stage_ev[h]);
+    }
+    if (s->stage_d) cudaFree(s->stage_d);
     for (cudaEvent_t &e : s->ev)
         if (e) cudaEventDestroy(e);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
@@ -931,6 +1048,19 @@ int md_create(md_sim **out, int n_replicas, const int *n_particles, const double
         md_destroy(s);
         return MD_ENOMEM;
     }
+    {
+        int nbig = 1;
+        for (int v : s->n) nbig = std::max(nbig, v);
+        s->stage_cap = std::min(nbig, kStageChunk);
+        const size_t sb = (size_t)s->stage_cap * stage_bytes_per_particle(R4);
+        for (int h = 0; h < 2; ++h)
+            if (cudaMallocHost((void **)&s->stage_h[h], sb) != cudaSuccess) {
+                s->stage_h[h] = nullptr;
+                md_destroy(s);
+                return MD_ENOMEM;
+            }
+        if (dallocb(s, &s->stage_d, sb)) { md_destroy(s); return MD_ENOMEM; }
+    }
     std::vector<int> prep(N);
     for (int r = 0; r < n_replicas; ++r)
         for (int k = 0; k < s->n[r]; ++k) prep[s->off[r] + k] = r;
@@ -971,6 +1101,8 @@ int md_create(md_sim **out, int n_replicas, const int *n_particles, const double
     ok = ok && cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) == cudaSuccess;
     ok = ok && cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) == cudaSuccess;
     for (int k = 0; ok && k < 3; ++k) ok = cudaEventCreate(&s->ev[k]) == cudaSuccess;
+    for (int h = 0; ok && h < 2; ++h)
+        ok = cudaEventCreateWithFlags(&s->stage_ev[h], cudaEventDisableTiming) == cudaSuccess;
     if (!ok) { md_destroy(s); return MD_ECUDA; }
     rc = configure_layout(s, true);
     if (rc) { md_destroy(s); return rc == MD_ENOMEM ? MD_ENOMEM : MD_ECUDA; }
@@ -1029,73 +1161,79 @@ int md_set_state(md_sim *s, int r, const double *pos, const int *type, const dou
         for (int c = 0; c < 3; ++c)
             if (!std::isfinite(pos[3 * k + c]) || !std::isfinite(vel[3 * k + c])) return MD_EINVAL;
     }
-    std::vector<double> x(n), y(n), z(n);
-    std::vector<int4> img(n);
-    std::vector<int> ids(n);
-    std::vector<unsigned char> mirror((size_t)n * s->r4), vv((size_t)n * s->r4);
-    double K = 0.0;
-    for (int k = 0; k < n; ++k) {
-        double w3[3];
-        int im3[3];
-        for (int c = 0; c < 3; ++c) {
-            double v = pos[3 * k + c];
-            double f = std::floor(v / L);
-            v -= f * L;
-            if (v >= L) { v -= L; f += 1.0; }
-            if (v < 0.0) { v += L; f -= 1.0; }
-            if (v >= L) v = 0.0;   // -tiny + L rounded up to L
-            w3[c] = v;
-            im3[c] = (int)f + (image ? image[3 * k + c] : 0);
-        }
-        img[k] = make_int4(im3[0], im3[1], im3[2], 0);
-        ids[k] = k;
-        if (s->precision == MD_FP64) {
-            x[k] = w3[0]; y[k] = w3[1]; z[k] = w3[2];
-            pack_pos(mirror, k, w3[0], w3[1], w3[2], type[k]);
-        } else {   // 64-bit fixed-point master (stored in the same 8 bytes) and its mirror
-            const uint64_t q[3] = {to_fixed64(w3[0], L), to_fixed64(w3[1], L),
-                                   to_fixed64(w3[2], L)};
-            std::memcpy(&x[k], &q[0], 8);
-            std::memcpy(&y[k], &q[1], 8);
-            std::memcpy(&z[k], &q[2], 8);
-            pack_mirror(mirror, k, q[0], q[1], q[2], type[k]);
-        }
-        double vs[3];
-        if (s->precision == MD_FP64) {
-            pack_v4<double>(vv, k, vel[3 * k], vel[3 * k + 1], vel[3 * k + 2], 0.0);
-            vs[0] = vel[3 * k]; vs[1] = vel[3 * k + 1]; vs[2] = vel[3 * k + 2];
-        } else {
-            pack_v4<float>(vv, k, vel[3 * k], vel[3 * k + 1], vel[3 * k + 2], 0.0);
-            vs[0] = (float)vel[3 * k]; vs[1] = (float)vel[3 * k + 1]; vs[2] = (float)vel[3 * k + 2];
-        }
-        K += 0.5 * s->mass[type[k]] * (vs[0] * vs[0] + vs[1] * vs[1] + vs[2] * vs[2]);
-    }
-    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(s, MD_ECUDA);
-    const int o = s->off[r];
-    const int cur = (int)(s->h_step & 1);
+    // Pack chunks of the replica into a pinned half of the staging area while the other half's
+    // copy runs; every copy and unpack kernel is ordered on the simulation's stream after the
+    // steps already queued, so no step in flight sees a partly written state.
     const size_t R4 = s->r4;
-    Buffers &b = s->b;
+    double K = 0.0;
+    for (int k0 = 0; k0 < n; k0 += s->stage_cap) {
+        const int cn = std::min(s->stage_cap, n - k0);
+        const int h = s->stage_k;
+        s->stage_k ^= 1;
+        if (cudaEventSynchronize(s->stage_ev[h]) != cudaSuccess) return fail(s, MD_ECUDA);
+        unsigned char *mir = s->stage_h[h];
+        unsigned char *vv = mir + (size_t)cn * R4;
+        int4 *img = (int4 *)(vv + (size_t)cn * R4);
+        unsigned char *xs = (unsigned char *)(img + cn);
+        unsigned char *ys = xs + (size_t)cn * 8, *zs = ys + (size_t)cn * 8;
+        for (int j = 0; j < cn; ++j) {
+            const int k = k0 + j;
+            double w3[3];
+            int im3[3];
+            for (int c = 0; c < 3; ++c) {
+                double v = pos[3 * k + c];
+                double f = 0.0;
+                if (!(v > 0.0 && v < L)) {   // (inside (0, L) the steps below return v, 0)
+                    f = std::floor(v / L);
+                    v -= f * L;
+                    if (v >= L) { v -= L; f += 1.0; }
+                    if (v < 0.0) { v += L; f -= 1.0; }
+                    if (v >= L) v = 0.0;   // -tiny + L rounded up to L
+                }
+                w3[c] = v;
+                im3[c] = (int)f + (image ? image[3 * k + c] : 0);
+            }
+            img[j] = make_int4(im3[0], im3[1], im3[2], 0);
+            if (s->precision == MD_FP64) {
+                std::memcpy(xs + 8 * (size_t)j, &w3[0], 8);
+                std::memcpy(ys + 8 * (size_t)j, &w3[1], 8);
+                std::memcpy(zs + 8 * (size_t)j, &w3[2], 8);
+                pack_pos(mir, j, w3[0], w3[1], w3[2], type[k]);
+            } else {   // 64-bit fixed-point master (stored in the same 8 bytes) and its mirror
+                const uint64_t q[3] = {to_fixed64(w3[0], L), to_fixed64(w3[1], L),
+                                       to_fixed64(w3[2], L)};
+                std::memcpy(xs + 8 * (size_t)j, &q[0], 8);
+                std::memcpy(ys + 8 * (size_t)j, &q[1], 8);
+                std::memcpy(zs + 8 * (size_t)j, &q[2], 8);
+                pack_mirror(mir, j, q[0], q[1], q[2], type[k]);
+            }
+            double vs[3];
+            if (s->precision == MD_FP64) {
+                pack_v4<double>(vv, j, vel[3 * k], vel[3 * k + 1], vel[3 * k + 2], 0.0);
+                vs[0] = vel[3 * k]; vs[1] = vel[3 * k + 1]; vs[2] = vel[3 * k + 2];
+            } else {
+                pack_v4<float>(vv, j, vel[3 * k], vel[3 * k + 1], vel[3 * k + 2], 0.0);
+                vs[0] = (float)vel[3 * k]; vs[1] = (float)vel[3 * k + 1];
+                vs[2] = (float)vel[3 * k + 2];
+            }
+            K += 0.5 * s->mass[type[k]] * (vs[0] * vs[0] + vs[1] * vs[1] + vs[2] * vs[2]);
+        }
+        const size_t bytes = (size_t)cn * (2 * R4 + 40);
+        if (cudaMemcpyAsync(s->stage_d, mir, bytes, cudaMemcpyHostToDevice, s->stream) !=
+                cudaSuccess ||
+            cudaEventRecord(s->stage_ev[h], s->stream) != cudaSuccess)
+            return fail(s, MD_ECUDA);
+        k_load_state<<<xfer_grid(cn), 256, 0, s->stream>>>(state_xfer(s, r, k0, cn));
+        if (cudaGetLastError() != cudaSuccess) return fail(s, MD_ECUDA);
+    }
     Thermo th;
     std::memset(&th, 0, sizeof(th));
     th.K_prev = K;
     host_next_factors(s, th, s->sys[r].K0);
-    const int one = 1, zero = 0;
-    bool ok = true;
-    ok = ok && cudaMemcpy((char *)b.pos[cur] + o * R4, mirror.data(), n * R4, cudaMemcpyHostToDevice) == cudaSuccess;
-    ok = ok && cudaMemcpy((char *)b.pos_build + o * R4, mirror.data(), n * R4, cudaMemcpyHostToDevice) == cudaSuccess;
-    ok = ok && cudaMemcpy(b.xd + o, x.data(), n * 8, cudaMemcpyHostToDevice) == cudaSuccess;
-    ok = ok && cudaMemcpy(b.yd + o, y.data(), n * 8, cudaMemcpyHostToDevice) == cudaSuccess;
-    ok = ok && cudaMemcpy(b.zd + o, z.data(), n * 8, cudaMemcpyHostToDevice) == cudaSuccess;
-    ok = ok && cudaMemcpy((char *)b.vel + o * R4, vv.data(), n * R4, cudaMemcpyHostToDevice) == cudaSuccess;
-    ok = ok && cudaMemcpy(b.img + o, img.data(), n * sizeof(int4), cudaMemcpyHostToDevice) == cudaSuccess;
-    ok = ok && cudaMemcpy(b.id + o, ids.data(), n * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
-    ok = ok && cudaMemset(b.nnb + o, 0, n * sizeof(int)) == cudaSuccess;
-    ok = ok && cudaMemcpy(b.th + r, &th, sizeof(th), cudaMemcpyHostToDevice) == cudaSuccess;
-    ok = ok && cudaMemcpy(need_now(s) + r, &one, sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
-    ok = ok && cudaMemcpy(b.moved + r, &zero, sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
-    ok = ok && cudaMemset(b.disp + 2 * r, 0, 2 * sizeof(unsigned)) == cudaSuccess;
-    ok = ok && cudaMemcpy(&b.ctrl->need_any, &one, sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
-    if (!ok) return fail(s, MD_ECUDA);
+    Buffers &b = s->b;
+    k_load_replica<<<1, 1, 0, s->stream>>>(th, b.th + r, need_now(s) + r, b.moved + r,
+                                           b.disp + 2 * r, b.ctrl);
+    if (cudaGetLastError() != cudaSuccess) return fail(s, MD_ECUDA);
     s->loaded[r] = 1;
     return MD_OK;
 }
@@ -1167,37 +1305,44 @@ int md_get_state(md_sim *s, int r, double *pos, int *image, double *vel) {
     if (rc) return rc;
     if (s->sticky) return s->sticky;
     if (!s->loaded[r]) return MD_ESTATE;
-    const int n = s->n[r], o = s->off[r];
+    const int n = s->n[r];
     const size_t R4 = s->r4;
-    std::vector<double> x(n), y(n), z(n);
-    std::vector<int4> img(n);
-    std::vector<int> ids(n);
-    std::vector<unsigned char> vv((size_t)n * R4);
-    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(s, MD_ECUDA);
-    const Buffers &b = s->b;
-    bool ok = cudaMemcpy(x.data(), b.xd + o, n * 8, cudaMemcpyDeviceToHost) == cudaSuccess;
-    ok = ok && cudaMemcpy(y.data(), b.yd + o, n * 8, cudaMemcpyDeviceToHost) == cudaSuccess;
-    ok = ok && cudaMemcpy(z.data(), b.zd + o, n * 8, cudaMemcpyDeviceToHost) == cudaSuccess;
-    ok = ok && cudaMemcpy(img.data(), b.img + o, n * sizeof(int4), cudaMemcpyDeviceToHost) == cudaSuccess;
-    ok = ok && cudaMemcpy(ids.data(), b.id + o, n * sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess;
-    ok = ok && cudaMemcpy(vv.data(), (char *)b.vel + o * R4, n * R4, cudaMemcpyDeviceToHost) == cudaSuccess;
-    if (!ok) return fail(s, MD_ECUDA);
-    if (s->precision == MD_MIXED)   // 64-bit fixed-point masters -> coordinates in [0, L)
-        for (int k = 0; k < n; ++k) {
-            uint64_t q[3];
-            std::memcpy(&q[0], &x[k], 8);
-            std::memcpy(&q[1], &y[k], 8);
-            std::memcpy(&q[2], &z[k], 8);
-            x[k] = from_fixed64(q[0], s->L[r]);
-            y[k] = from_fixed64(q[1], s->L[r]);
-            z[k] = from_fixed64(q[2], s->L[r]);
+    for (int k0 = 0; k0 < n; k0 += s->stage_cap) {
+        const int cn = std::min(s->stage_cap, n - k0);
+        // slots k0 .. k0 + cn - 1 packed on the device (after the queued steps), one copy back
+        const int h = s->stage_k;
+        k_save_state<<<xfer_grid(cn), 256, 0, s->stream>>>(state_xfer(s, r, k0, cn));
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(s->stage_h[h], s->stage_d, (size_t)cn * (R4 + 44),
+                            cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+            cudaStreamSynchronize(s->stream) != cudaSuccess)
+            return fail(s, MD_ECUDA);
+        const unsigned char *vv = s->stage_h[h];
+        const int4 *img = (const int4 *)(vv + (size_t)cn * R4);
+        const unsigned char *xs = (const unsigned char *)(img + cn);
+        const unsigned char *ys = xs + (size_t)cn * 8, *zs = ys + (size_t)cn * 8;
+        const int *ids = (const int *)(zs + (size_t)cn * 8);
+        for (int j = 0; j < cn; ++j) {
+            const int u = ids[j];
+            if (u < 0 || u >= n) return fail(s, MD_ECUDA);
+            double p3[3];
+            if (s->precision == MD_MIXED) {   // 64-bit fixed-point masters -> [0, L)
+                uint64_t q[3];
+                std::memcpy(&q[0], xs + 8 * (size_t)j, 8);
+                std::memcpy(&q[1], ys + 8 * (size_t)j, 8);
+                std::memcpy(&q[2], zs + 8 * (size_t)j, 8);
+                for (int c = 0; c < 3; ++c) p3[c] = from_fixed64(q[c], s->L[r]);
+            } else {
+                std::memcpy(&p3[0], xs + 8 * (size_t)j, 8);
+                std::memcpy(&p3[1], ys + 8 * (size_t)j, 8);
+                std::memcpy(&p3[2], zs + 8 * (size_t)j, 8);
+            }
+            if (pos) { pos[3 * u] = p3[0]; pos[3 * u + 1] = p3[1]; pos[3 * u + 2] = p3[2]; }
+            if (image) {
+                image[3 * u] = img[j].x; image[3 * u + 1] = img[j].y; image[3 * u + 2] = img[j].z;
+            }
+            if (vel) unpack_v4(s, vv, j, vel + 3 * u);
         }
-    for (int k = 0; k < n; ++k) {
-        const int u = ids[k];
-        if (u < 0 || u >= n) return fail(s, MD_ECUDA);
-        if (pos) { pos[3 * u] = x[k]; pos[3 * u + 1] = y[k]; pos[3 * u + 2] = z[k]; }
-        if (image) { image[3 * u] = img[k].x; image[3 * u + 1] = img[k].y; image[3 * u + 2] = img[k].z; }
-        if (vel) unpack_v4(s, vv, k, vel + 3 * u);
     }
     return MD_OK;
 }
