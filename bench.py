@@ -2,10 +2,11 @@
 
 Workload (default, N=1): the batched Kob-Andersen ensemble -- 512 independent replicas with
 N_r drawn uniformly from 512..4096 (seed 1004), rho = 1.2, Nose-Hoover NVT at T = 0.8,
-dt = 0.0025, skin 0.3, CUDA-graph blocks of 100 steps, kernel shape chosen by the autotuner.
+dt = 0.0025, skin 0.3 (tuned), kernel shape chosen by the autotuner; the timed steps run as CUDA-graph
+blocks that cut them into five equal segments (at most 100 steps a block).
 One bench step = one MD timestep of every replica (force + integrate + skin check + on-device
 rebuild where needed + FP64 reductions).  Inputs are synthetic (seeded), resident in HBM.
-The ensemble's working set (neighbour list ~0.45 GB) exceeds the 129 MB L2, so no flush is
+The ensemble's working set (neighbour list ~0.5 GB) exceeds the 129 MB L2, so no flush is
 needed between timed steps.
 
 Also reported in the same line: the same replicas run one after another with plain kernel
