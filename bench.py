@@ -368,7 +368,8 @@ def time_single_system(name, stream_obj, steps, warmup, peaks=None, p_fp32=None)
     if peaks is not None:
         out["roofline"] = step_roofline(sim, wl, peaks, p_fp32)
     st = sim.stats()
-    out.update(tuning=list(sim.get_tuning()), rebuild_passes=st["rebuild_passes"])
+    out.update(tuning=list(sim.get_tuning()), rebuild_passes=st["rebuild_passes"],
+               kernel_path={1: "grid", 2: "replica", 3: "staged", 4: "lean"}.get(st["path"]))
     sim.close()
     return out
 

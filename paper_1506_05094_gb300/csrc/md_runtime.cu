@@ -2157,12 +2157,19 @@ extern "C" int md_autotune(md_sim *s, const char *cache_path, int steps, int fla
         }
         if (best_b >= 1.10 * best) break;
     }
-    // the register cap again at the best shape (its benefit depends on the block and t_p)
+    // the register cap again at the best shape and the blocks beside it (its benefit depends on
+    // the block and t_p: the capped kernel fits more CTAs of a given block on an SM)
     if (s->path == 1 || s->path == 4) {
-        const int other = s->path == 1 ? 4 : 1, mine = s->path;
+        const int mine = s->path, other = mine == 1 ? 4 : 1;
+        const int b0 = best_block;
+        int best_path = mine;
         s->path = other;
-        if ((rc = trial(best_tp, best_block, best_reach, best_lanes, &t))) return rc;
-        if (t < best) best = t; else s->path = mine;
+        for (int b : {b0, b0 / 2, b0 * 2}) {
+            if (b < 64 || b > 1024 || b < best_tp) continue;
+            if ((rc = trial(best_tp, b, best_reach, best_lanes, &t))) return rc;
+            if (t < best) { best = t; best_block = b; best_path = other; }
+        }
+        s->path = best_path;
     }
     // phase III: lanes per particle of the list build (single minimum: walk down, then up);
     // the replica-resident kernel is built for 8 and 32 lanes
