@@ -156,3 +156,37 @@ def test_perfect_crystal_at_rest():
     Ur = oracle.forces(pos, st.types, L, LJ)[3]
     assert e["U"] == pytest.approx(Ur, rel=1e-6)
     assert U0 == pytest.approx(Ur, rel=1e-6)
+
+
+def test_state_round_trip_through_several_staging_chunks():
+    """md_set_state then md_get_state with no step between, for replicas larger than one staging
+    chunk (65536 particles) beside small ones, from coordinates in other periodic images: the
+    positions come back wrapped into [0, L) to within the 2^-64 L master resolution, the images
+    carry the wraps, the velocities are the FP32 values, and every particle returns in user
+    order."""
+    big = synth.lj_fcc_state(4 * 32 * 32 * 36, 0.8442, 0.72, 77)   # 147456: three chunks
+    small = ka(900, seed=78)
+    rng = np.random.default_rng(79)
+    shifts = [rng.integers(-3, 4, size=st.pos.shape) for st in (big, small)]
+    # (pos + k L) rounds to 2^-52 of |k L|: the wrapped coordinate carries that rounding
+    with make_sim(synth.lj_model(), [big]) as sim:
+        pos_in = big.pos + shifts[0] * big.L
+        sim.set_state(0, pos_in, big.types, big.vel)
+        pos, img, vel = sim.get_state(0)
+    wrapped = big.pos - np.floor(big.pos / big.L) * big.L
+    assert np.all((pos >= 0) & (pos < big.L))
+    np.testing.assert_allclose(pos, wrapped, rtol=0, atol=16 * big.L * 2.0 ** -52)
+    np.testing.assert_array_equal(img, shifts[0] + np.floor(big.pos / big.L).astype(int))
+    np.testing.assert_array_equal(vel, f32(big.vel))
+    with make_sim(synth.ka_model(), [small, big]) as sim:
+        sim.set_state(0, small.pos + shifts[1] * small.L, small.types, small.vel)
+        sim.set_state(1, pos_in, big.types, big.vel)
+        p0, i0, v0 = sim.get_state(0)
+        p1, i1, v1 = sim.get_state(1)
+    np.testing.assert_allclose(p1, pos, rtol=0, atol=0)
+    np.testing.assert_array_equal(i1, img)
+    np.testing.assert_array_equal(v1, vel)
+    w0 = small.pos - np.floor(small.pos / small.L) * small.L
+    np.testing.assert_allclose(p0, w0, rtol=0, atol=16 * small.L * 2.0 ** -52)
+    np.testing.assert_array_equal(i0, shifts[1] + np.floor(small.pos / small.L).astype(int))
+    np.testing.assert_array_equal(v0, f32(small.vel))

@@ -7,7 +7,8 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import f32, make_sim
+from gpu_util import dev_pos, f32, make_sim, rel_rms
+from paper_1506_05094_gb300 import md
 
 pytestmark = pytest.mark.gpu
 
@@ -167,3 +168,58 @@ def test_ka_ensemble64_nve_1e6_steps_per_replica_drift():
           f"+- {se_win:.1e}, FP64 oracle drift {d_or:.3e} +- {se_or:.1e}")
     assert abs(d_win - d_or) <= 5 * np.hypot(se_win, se_or) + 2e-7
     assert np.abs(d_all).max() < 1e-5
+
+
+def test_ka_ensemble512_bench_configuration_sampled_against_oracle():
+    """The timed workload at full size (512 KA replicas, 1,153,755 particles) in the launch
+    configuration the bench times: t_p = 1, block 256, reach 2, the list build with one warp per
+    cell, split graph steps of 4 steps, skin 0.27, NVT T = 0.8.  After 800 steps, in which every
+    replica passes through its own skin-triggered rebuilds, sampled replicas (the smallest, the
+    largest and seven drawn with a seed) are checked against the oracle on the state read back:
+    forces to 1e-5 relative RMS, U to 1e-6, W to 1e-6 of sum |w_i|, every u_i and w_i.  On every
+    replica the total momentum stays ~0.  The Nose-Hoover H drifts while a random start relaxes
+    (its close contacts make the first steps stiff, and the shifted potential's force jump at rc
+    conserves nothing exactly): its change over steps 400-800 is compared with the FP64
+    oracle's for the smallest replica, the replica whose H moves most and one drawn with a seed."""
+    wl = synth.workload("ka_ensemble512")
+    R = len(wl.states)
+    n = np.array([st.n for st in wl.states], dtype=float)
+    with make_sim(wl.model, wl.states, skin=0.27, integrator="nvt", dt=wl.dt, T=wl.T,
+                  tau=wl.tau, tuning=(1, 256, 2, md.MD_BUILD_CELL), graph_block=4) as sim:
+        sim.step(400)
+        H0 = np.array([sim.energies(r)["H"] for r in range(R)])
+        b0 = sim.stats()["replica_rebuilds"]
+        sim.step(400)
+        e = [sim.energies(r) for r in range(R)]
+        assert sim.stats()["replica_rebuilds"] - b0 > R   # rebuilds ran inside the steps
+        dH = (np.array([x["H"] for x in e]) - H0) / n
+        p = np.array([np.linalg.norm(x["sum_p"]) for x in e])
+        assert p.max() < 5e-3, p.max()
+        rng = np.random.default_rng(512)
+        sample = sorted({int(np.argmin(n)), int(np.argmax(n))} |
+                        set(rng.choice(R, 7, replace=False).tolist()))
+        worst = 0.0
+        for r in sample:
+            st = wl.states[r]
+            pos, _, _ = sim.get_state(r)
+            f, u, w = sim.forces(r)
+            fr, ur, wr, U, W = oracle.forces(dev_pos(pos, st.L), st.types, st.L, wl.model)
+            worst = max(worst, rel_rms(f, fr))
+            assert rel_rms(f, fr) <= 1e-5, (r, rel_rms(f, fr))
+            assert abs(u.sum() - U) <= 1e-6 * abs(U), (r, u.sum(), U)
+            assert abs(w.sum() - W) <= 1e-6 * np.abs(wr).sum(), (r, w.sum(), W)
+            np.testing.assert_allclose(u, ur, rtol=2e-5, atol=2e-6 * np.abs(ur).max())
+            np.testing.assert_allclose(w, wr, rtol=2e-5, atol=2e-6 * np.abs(wr).max())
+    print(f"ensemble512 sampled replicas {sample}: worst force rel RMS {worst:.2e}; "
+          f"max |sum p| {p.max():.3e}")
+    rows = []
+    for r in sorted({int(np.argmin(n)), int(np.argmax(np.abs(dH))), int(rng.integers(R))}):
+        st = wl.states[r]
+        ref = oracle.Run(st.pos, f32(st.vel), st.types, st.L, wl.model, "nvt", wl.dt, T=wl.T,
+                         tau=wl.tau, cells=True)
+        h400 = ref.run(400)[-1, 9]
+        h800 = ref.run(400)[-1, 9]
+        d_or = (h800 - h400) / st.n
+        rows.append(f"replica {r} (N = {st.n}): GPU {dH[r]:+.3e}, FP64 oracle {d_or:+.3e}")
+        assert abs(dH[r] - d_or) <= 0.1 * abs(d_or) + 5e-4, (r, dH[r], d_or)
+    print("ensemble512 H change per particle over steps 400-800: " + "; ".join(rows))
