@@ -727,40 +727,95 @@ void unpack_v4(const md_sim *s, const std::vector<unsigned char> &src, size_t k,
 }
 
 // ---- packed state transfers
-// One chunk of a replica's state in the staging area, particles k0 .. k0 + n - 1 (user order on
-// the way in, slot order on the way out).  In: mirror records, velocity records, image counters,
-// then the x, y and z masters (8 bytes each: doubles, or 64-bit fixed point).  Out: velocity
-// records, image counters, x, y, z masters, user ids.  Records are R4 bytes (r4w int4 words).
+// md_set_state copies the caller's arrays for a chunk of user indices k0 .. k0 + n - 1 into the
+// staging area as they are (positions, velocities, types, images: 64 bytes a particle) and one
+// kernel wraps, quantises and packs them into the replica's slots -- the same IEEE steps as the
+// host helpers above (explicit roundings, no contraction), so the device holds the same bits.
+// md_get_state packs on the device: for a replica that fits one chunk, positions (dequantised),
+// velocities and images in user order (60 bytes a particle), so the host only copies them out;
+// a larger replica comes out in slot order, chunk by chunk, with its ids (velocity records,
+// image counters, the x, y, z masters, ids) and is unpacked on the host.
 constexpr int kStageChunk = 1 << 16;
 size_t stage_bytes_per_particle(size_t R4) { return 2 * R4 + 48; }
 
 struct StateXfer {
     void *stage;
     int n, k0, o, r4w;
+    int mixed, has_image;
+    double L;
     int4 *pos, *pos_build, *vel;
     unsigned long long *x, *y, *z;
     int4 *img;
     int *id, *nnb;
 };
 
+// wrap of one coordinate into [0, L) with its image shift (the host's steps in md_set_state)
+__device__ double wrap_coordinate(double v, double L, double &f) {
+    f = 0.0;
+    if (!(v > 0.0 && v < L)) {
+        f = floor(__ddiv_rn(v, L));
+        v = __dsub_rn(v, __dmul_rn(f, L));
+        if (v >= L) { v = __dsub_rn(v, L); f = __dadd_rn(f, 1.0); }
+        if (v < 0.0) { v = __dadd_rn(v, L); f = __dsub_rn(f, 1.0); }
+        if (v >= L) v = 0.0;
+    }
+    return v;
+}
+// to_fixed64 / from_fixed64 / mirror32 of the host, on the device
+__device__ unsigned long long fixed64_of(double x, double L) {
+    double q = __dmul_rn(__ddiv_rn(x, L), 18446744073709551616.0);
+    if (q < 4503599627370496.0) q = rint(q);
+    if (!(q < 18446744073709551616.0)) return 0ull;
+    return q <= 0.0 ? 0ull : __double2ull_rz(q);
+}
+__device__ double coordinate_of(unsigned long long q, double L) {
+    const double x = __dmul_rn(__dmul_rn(__ull2double_rn(q), 5.421010862427522170037264e-20), L);
+    return x < L ? x : nextafter(L, 0.0);
+}
+__device__ int mirror_of(unsigned long long q) {
+    return (int)(unsigned)((q + 0x80000000ull) >> 32);
+}
+
 __global__ void k_load_state(const StateXfer t) {
-    const int4 *mir = (const int4 *)t.stage;
-    const int4 *vel = mir + (size_t)t.n * t.r4w;
-    const int4 *img = vel + (size_t)t.n * t.r4w;
-    const unsigned long long *x = (const unsigned long long *)(img + t.n);
-    const unsigned long long *y = x + t.n, *z = y + t.n;
+    const double *pos = (const double *)t.stage;
+    const double *vel = pos + 3 * (size_t)t.n;
+    const int *type = (const int *)(vel + 3 * (size_t)t.n);
+    const int *image = type + t.n;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < t.n; k += gridDim.x * blockDim.x) {
         const size_t d = (size_t)t.o + t.k0 + k;
-        for (int w = 0; w < t.r4w; ++w) {
-            const int4 m = mir[(size_t)k * t.r4w + w];
-            t.pos[d * t.r4w + w] = m;
-            t.pos_build[d * t.r4w + w] = m;
-            t.vel[d * t.r4w + w] = vel[(size_t)k * t.r4w + w];
+        double w[3], f[3];
+        for (int c = 0; c < 3; ++c) w[c] = wrap_coordinate(pos[3 * (size_t)k + c], t.L, f[c]);
+        int im[3];
+        for (int c = 0; c < 3; ++c)
+            im[c] = (int)f[c] + (t.has_image ? image[3 * (size_t)k + c] : 0);
+        t.img[d] = make_int4(im[0], im[1], im[2], 0);
+        const int ty = type[k];
+        const double *v = vel + 3 * (size_t)k;
+        if (t.mixed) {
+            const unsigned long long q[3] = {fixed64_of(w[0], t.L), fixed64_of(w[1], t.L),
+                                             fixed64_of(w[2], t.L)};
+            const int4 m = make_int4(mirror_of(q[0]), mirror_of(q[1]), mirror_of(q[2]), ty);
+            t.pos[d] = m;
+            t.pos_build[d] = m;
+            t.x[d] = q[0];
+            t.y[d] = q[1];
+            t.z[d] = q[2];
+            const float4 vf = make_float4(__double2float_rn(v[0]), __double2float_rn(v[1]),
+                                          __double2float_rn(v[2]), 0.f);
+            t.vel[d] = *(const int4 *)&vf;
+        } else {
+            const double4_32a m = make_double4_32a(w[0], w[1], w[2],
+                                                   __longlong_as_double((long long)ty));
+            const double4_32a vd = make_double4_32a(v[0], v[1], v[2], 0.0);
+            for (int q = 0; q < 2; ++q) {
+                t.pos[2 * d + q] = ((const int4 *)&m)[q];
+                t.pos_build[2 * d + q] = ((const int4 *)&m)[q];
+                t.vel[2 * d + q] = ((const int4 *)&vd)[q];
+            }
+            t.x[d] = (unsigned long long)__double_as_longlong(w[0]);
+            t.y[d] = (unsigned long long)__double_as_longlong(w[1]);
+            t.z[d] = (unsigned long long)__double_as_longlong(w[2]);
         }
-        t.x[d] = x[k];
-        t.y[d] = y[k];
-        t.z[d] = z[k];
-        t.img[d] = img[k];
         t.id[d] = t.k0 + k;
         t.nnb[d] = 0;
     }
@@ -778,6 +833,44 @@ __global__ void k_load_replica(const Thermo th, Thermo *th_dst, int *need, int *
     ctrl->need_any = 1;
 }
 
+// a whole replica (t.k0 = 0, t.n = its size) in user order: positions in [0, L), velocities,
+// images
+__global__ void k_save_user(const StateXfer t) {
+    double *pos = (double *)t.stage;
+    double *vel = pos + 3 * (size_t)t.n;
+    int *image = (int *)(vel + 3 * (size_t)t.n);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < t.n; k += gridDim.x * blockDim.x) {
+        const size_t d = (size_t)t.o + k;
+        const int u = t.id[d];
+        if (u < 0 || u >= t.n) continue;
+        double p3[3], v3[3];
+        if (t.mixed) {
+            p3[0] = coordinate_of(t.x[d], t.L);
+            p3[1] = coordinate_of(t.y[d], t.L);
+            p3[2] = coordinate_of(t.z[d], t.L);
+            const int4 vi = t.vel[d];
+            const float4 vf = *(const float4 *)&vi;
+            v3[0] = vf.x; v3[1] = vf.y; v3[2] = vf.z;
+        } else {
+            p3[0] = __longlong_as_double((long long)t.x[d]);
+            p3[1] = __longlong_as_double((long long)t.y[d]);
+            p3[2] = __longlong_as_double((long long)t.z[d]);
+            int4 raw[2] = {t.vel[2 * d], t.vel[2 * d + 1]};
+            const double4_32a vd = *(const double4_32a *)raw;
+            v3[0] = vd.x; v3[1] = vd.y; v3[2] = vd.z;
+        }
+        const int4 im = t.img[d];
+        for (int c = 0; c < 3; ++c) {
+            pos[3 * (size_t)u + c] = p3[c];
+            vel[3 * (size_t)u + c] = v3[c];
+        }
+        image[3 * (size_t)u] = im.x;
+        image[3 * (size_t)u + 1] = im.y;
+        image[3 * (size_t)u + 2] = im.z;
+    }
+}
+
+// a chunk of slots k0 .. k0 + n - 1 as stored, with the ids (replicas larger than one chunk)
 __global__ void k_save_state(const StateXfer t) {
     int4 *vel = (int4 *)t.stage;
     int4 *img = vel + (size_t)t.n * t.r4w;
@@ -802,6 +895,9 @@ StateXfer state_xfer(md_sim *s, int r, int k0, int n) {
     t.k0 = k0;
     t.o = s->off[r];
     t.r4w = (int)(s->r4 / 16);
+    t.mixed = s->precision == MD_MIXED ? 1 : 0;
+    t.has_image = 0;
+    t.L = s->L[r];
     t.pos = (int4 *)s->b.pos[s->h_step & 1];
     t.pos_build = (int4 *)s->b.pos_build;
     t.vel = (int4 *)s->b.vel;
@@ -1155,75 +1251,42 @@ int md_set_state(md_sim *s, int r, const double *pos, const int *type, const dou
     if (s->sticky) return s->sticky;
     if (!pos || !type || !vel) return MD_EINVAL;
     const int n = s->n[r];
-    const double L = s->L[r];
+    // validation and the kinetic energy of the FP32 (mixed) or FP64 velocities, in user order
+    double K = 0.0;
     for (int k = 0; k < n; ++k) {
         if (type[k] < 0 || type[k] >= s->nt) return MD_EINVAL;
         for (int c = 0; c < 3; ++c)
             if (!std::isfinite(pos[3 * k + c]) || !std::isfinite(vel[3 * k + c])) return MD_EINVAL;
+        double vs[3];
+        for (int c = 0; c < 3; ++c)
+            vs[c] = s->precision == MD_FP64 ? vel[3 * k + c] : (double)(float)vel[3 * k + c];
+        K += 0.5 * s->mass[type[k]] * (vs[0] * vs[0] + vs[1] * vs[1] + vs[2] * vs[2]);
     }
-    // Pack chunks of the replica into a pinned half of the staging area while the other half's
-    // copy runs; every copy and unpack kernel is ordered on the simulation's stream after the
-    // steps already queued, so no step in flight sees a partly written state.
-    const size_t R4 = s->r4;
-    double K = 0.0;
+    // Chunks of the caller's arrays go into a pinned half of the staging area while the other
+    // half's copy may still run; each copy and its unpack kernel are ordered on the
+    // simulation's stream after the steps already queued, so no step in flight sees a partly
+    // written state.
     for (int k0 = 0; k0 < n; k0 += s->stage_cap) {
         const int cn = std::min(s->stage_cap, n - k0);
         const int h = s->stage_k;
         s->stage_k ^= 1;
         if (cudaEventSynchronize(s->stage_ev[h]) != cudaSuccess) return fail(s, MD_ECUDA);
-        unsigned char *mir = s->stage_h[h];
-        unsigned char *vv = mir + (size_t)cn * R4;
-        int4 *img = (int4 *)(vv + (size_t)cn * R4);
-        unsigned char *xs = (unsigned char *)(img + cn);
-        unsigned char *ys = xs + (size_t)cn * 8, *zs = ys + (size_t)cn * 8;
-        for (int j = 0; j < cn; ++j) {
-            const int k = k0 + j;
-            double w3[3];
-            int im3[3];
-            for (int c = 0; c < 3; ++c) {
-                double v = pos[3 * k + c];
-                double f = 0.0;
-                if (!(v > 0.0 && v < L)) {   // (inside (0, L) the steps below return v, 0)
-                    f = std::floor(v / L);
-                    v -= f * L;
-                    if (v >= L) { v -= L; f += 1.0; }
-                    if (v < 0.0) { v += L; f -= 1.0; }
-                    if (v >= L) v = 0.0;   // -tiny + L rounded up to L
-                }
-                w3[c] = v;
-                im3[c] = (int)f + (image ? image[3 * k + c] : 0);
-            }
-            img[j] = make_int4(im3[0], im3[1], im3[2], 0);
-            if (s->precision == MD_FP64) {
-                std::memcpy(xs + 8 * (size_t)j, &w3[0], 8);
-                std::memcpy(ys + 8 * (size_t)j, &w3[1], 8);
-                std::memcpy(zs + 8 * (size_t)j, &w3[2], 8);
-                pack_pos(mir, j, w3[0], w3[1], w3[2], type[k]);
-            } else {   // 64-bit fixed-point master (stored in the same 8 bytes) and its mirror
-                const uint64_t q[3] = {to_fixed64(w3[0], L), to_fixed64(w3[1], L),
-                                       to_fixed64(w3[2], L)};
-                std::memcpy(xs + 8 * (size_t)j, &q[0], 8);
-                std::memcpy(ys + 8 * (size_t)j, &q[1], 8);
-                std::memcpy(zs + 8 * (size_t)j, &q[2], 8);
-                pack_mirror(mir, j, q[0], q[1], q[2], type[k]);
-            }
-            double vs[3];
-            if (s->precision == MD_FP64) {
-                pack_v4<double>(vv, j, vel[3 * k], vel[3 * k + 1], vel[3 * k + 2], 0.0);
-                vs[0] = vel[3 * k]; vs[1] = vel[3 * k + 1]; vs[2] = vel[3 * k + 2];
-            } else {
-                pack_v4<float>(vv, j, vel[3 * k], vel[3 * k + 1], vel[3 * k + 2], 0.0);
-                vs[0] = (float)vel[3 * k]; vs[1] = (float)vel[3 * k + 1];
-                vs[2] = (float)vel[3 * k + 2];
-            }
-            K += 0.5 * s->mass[type[k]] * (vs[0] * vs[0] + vs[1] * vs[1] + vs[2] * vs[2]);
+        unsigned char *st = s->stage_h[h];
+        std::memcpy(st, pos + 3 * (size_t)k0, 24 * (size_t)cn);
+        std::memcpy(st + 24 * (size_t)cn, vel + 3 * (size_t)k0, 24 * (size_t)cn);
+        std::memcpy(st + 48 * (size_t)cn, type + k0, 4 * (size_t)cn);
+        size_t bytes = 52 * (size_t)cn;
+        if (image) {
+            std::memcpy(st + bytes, image + 3 * (size_t)k0, 12 * (size_t)cn);
+            bytes += 12 * (size_t)cn;
         }
-        const size_t bytes = (size_t)cn * (2 * R4 + 40);
-        if (cudaMemcpyAsync(s->stage_d, mir, bytes, cudaMemcpyHostToDevice, s->stream) !=
+        if (cudaMemcpyAsync(s->stage_d, st, bytes, cudaMemcpyHostToDevice, s->stream) !=
                 cudaSuccess ||
             cudaEventRecord(s->stage_ev[h], s->stream) != cudaSuccess)
             return fail(s, MD_ECUDA);
-        k_load_state<<<xfer_grid(cn), 256, 0, s->stream>>>(state_xfer(s, r, k0, cn));
+        StateXfer t = state_xfer(s, r, k0, cn);
+        t.has_image = image ? 1 : 0;
+        k_load_state<<<xfer_grid(cn), 256, 0, s->stream>>>(t);
         if (cudaGetLastError() != cudaSuccess) return fail(s, MD_ECUDA);
     }
     Thermo th;
@@ -1307,6 +1370,20 @@ int md_get_state(md_sim *s, int r, double *pos, int *image, double *vel) {
     if (!s->loaded[r]) return MD_ESTATE;
     const int n = s->n[r];
     const size_t R4 = s->r4;
+    if (n <= s->stage_cap) {   // one chunk: packed in user order on the device, copied out
+        const int h = s->stage_k;
+        k_save_user<<<xfer_grid(n), 256, 0, s->stream>>>(state_xfer(s, r, 0, n));
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(s->stage_h[h], s->stage_d, 60 * (size_t)n, cudaMemcpyDeviceToHost,
+                            s->stream) != cudaSuccess ||
+            cudaStreamSynchronize(s->stream) != cudaSuccess)
+            return fail(s, MD_ECUDA);
+        const unsigned char *st = s->stage_h[h];
+        if (pos) std::memcpy(pos, st, 24 * (size_t)n);
+        if (vel) std::memcpy(vel, st + 24 * (size_t)n, 24 * (size_t)n);
+        if (image) std::memcpy(image, st + 48 * (size_t)n, 12 * (size_t)n);
+        return MD_OK;
+    }
     for (int k0 = 0; k0 < n; k0 += s->stage_cap) {
         const int cn = std::min(s->stage_cap, n - k0);
         // slots k0 .. k0 + cn - 1 packed on the device (after the queued steps), one copy back
