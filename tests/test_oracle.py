@@ -450,3 +450,42 @@ def test_salt_neighbour_count_matches_density():
     _, counts = oracle.neighbors_fp64(s.pos, s.types, s.L, SALT, 0.3, maxn=1)
     expect = 0.3677 * 4.0 / 3.0 * math.pi * 6.3 ** 3
     assert counts.mean() == pytest.approx(expect, rel=0.03)
+
+
+def test_cell_stencil_search_volume_ratio():
+    """Sec. 7 (footnote): cells of edge (rc + s)/2 with a 5x5x5 stencil search (125/8)/27 = 0.58
+    of the volume searched with cells of edge rc + s and a 3x3x3 stencil.  Counted here on a
+    seeded uniform configuration (the candidates each particle visits in either stencil), and
+    both stencils hold every pair within rc + s (checked against brute force)."""
+    rng = np.random.default_rng(2015)
+    rcs, n_edge = 2.8, 8
+    L = n_edge * rcs
+    pos = rng.uniform(0, L, size=(3000, 3))
+
+    def candidates(reach):
+        nc = n_edge * reach                              # cell edge (rc + s) / reach
+        cell = np.floor(pos / (L / nc)).astype(int) % nc
+        occ = {}
+        for i, c in enumerate(map(tuple, cell)):
+            occ.setdefault(c, []).append(i)
+        offs = range(-reach, reach + 1)
+        visited, total = [], 0
+        for i, c in enumerate(map(tuple, cell)):
+            got = []
+            for dx in offs:
+                for dy in offs:
+                    for dz in offs:
+                        got += occ.get(((c[0] + dx) % nc, (c[1] + dy) % nc, (c[2] + dz) % nc), [])
+            total += len(got)
+            visited.append(set(got))
+        return total, visited
+
+    t1, v1 = candidates(1)
+    t2, v2 = candidates(2)
+    assert t2 / t1 == pytest.approx((125 / 8) / 27, rel=0.02)
+    d = pos[:, None, :] - pos[None, :, :]
+    d -= L * np.round(d / L)
+    near = (d ** 2).sum(-1) < rcs ** 2
+    for i in range(0, len(pos), 97):
+        want = set(np.flatnonzero(near[i]).tolist())
+        assert want <= v1[i] and want <= v2[i]
