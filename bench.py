@@ -566,6 +566,8 @@ def main():
     # no graph was captured or instantiated inside the timed region
     graph_builds_timed = st1["graph_builds"] - st0["graph_builds"]
     assert graph_builds_timed == 0, graph_builds_timed
+    # replicas rebuilt per timed step (the rebuild work the steps carried)
+    rebuilds_per_step = (st1["replica_rebuilds"] - st0["replica_rebuilds"]) / args.steps
     ms_max = rep.max_over_ranks(ms, device="cuda")
     value = rep.job_throughput(n_total, world, args.steps, ms_max)
     # five repeats inside the timed region: consecutive fifths of the K steps
@@ -714,7 +716,8 @@ def main():
                                   % (ws_bytes / 1e9)),
                            "parallelism": f"replicas x{world}"},
                 "clocks": clocks, "gpu_launches": gpu_launches, "roofline": roofline,
-                "repeats": repeats, "graph_builds_in_timed_region": graph_builds_timed}
+                "repeats": repeats, "graph_builds_in_timed_region": graph_builds_timed,
+                "replica_rebuilds_per_step": rebuilds_per_step}
         line.update(extras)
         if "e2e" not in line:
             line["e2e"] = None
