@@ -163,8 +163,8 @@ def test_state_round_trip_through_several_staging_chunks():
     """md_set_state then md_get_state with no step between, for replicas larger than one staging
     chunk (65536 particles) beside small ones, from coordinates in other periodic images: the
     positions come back wrapped into [0, L) to within the 2^-64 L master resolution, the images
-    carry the wraps, the velocities are the FP32 values, and every particle returns in user
-    order."""
+    carry the wraps (plus the images passed in), the velocities are the FP32 values, and every
+    particle returns in user order."""
     big = synth.lj_fcc_state(4 * 32 * 32 * 36, 0.8442, 0.72, 77)   # 147456: three chunks
     small = ka(900, seed=78)
     rng = np.random.default_rng(79)
@@ -179,8 +179,9 @@ def test_state_round_trip_through_several_staging_chunks():
     np.testing.assert_allclose(pos, wrapped, rtol=0, atol=16 * big.L * 2.0 ** -52)
     np.testing.assert_array_equal(img, shifts[0] + np.floor(big.pos / big.L).astype(int))
     np.testing.assert_array_equal(vel, f32(big.vel))
+    base = rng.integers(-50, 51, size=small.pos.shape).astype(np.int32)   # caller's images
     with make_sim(synth.ka_model(), [small, big]) as sim:
-        sim.set_state(0, small.pos + shifts[1] * small.L, small.types, small.vel)
+        sim.set_state(0, small.pos + shifts[1] * small.L, small.types, small.vel, image=base)
         sim.set_state(1, pos_in, big.types, big.vel)
         p0, i0, v0 = sim.get_state(0)
         p1, i1, v1 = sim.get_state(1)
@@ -189,7 +190,7 @@ def test_state_round_trip_through_several_staging_chunks():
     np.testing.assert_array_equal(v1, vel)
     w0 = small.pos - np.floor(small.pos / small.L) * small.L
     np.testing.assert_allclose(p0, w0, rtol=0, atol=16 * small.L * 2.0 ** -52)
-    np.testing.assert_array_equal(i0, shifts[1] + np.floor(small.pos / small.L).astype(int))
+    np.testing.assert_array_equal(i0, base + shifts[1] + np.floor(small.pos / small.L).astype(int))
     np.testing.assert_array_equal(v0, f32(small.vel))
 
 
